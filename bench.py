@@ -1,0 +1,324 @@
+"""Benchmark: Eikonal solves per second on one GB300, as Mpoints/s and HBM roofline fraction.
+
+One step = one full solve of the block-based restarted narrow-band method
+(initialisation, every restart's march and exchange, activation) on the 1024^3
+workload: node grid h = 1/1023, F = exp(g) with g a smooth random field (std
+0.5, correlation length 0.05), point source at the centre, FP32 storage with
+the FP64 root fallback.  Inputs are resident in HBM when the timed region
+starts; they are larger than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own instance of the workload
+(independent problems, no collective on the data path: weak scaling); rank 0
+prints one JSON line with the whole-job throughput.  --impl reference times
+the FP64 CPU oracle on a bounded sample of the same workload family.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Eikonal Mpoints/s at 512^3/1024^3 + HBM roofline %; learned vs fixed stride"
+ALGO_BYTES_PER_POINT = {"fp32": 8, "fp64": 16}      # read F once + write psi once
+KERNELS_PER_SOLVE = 4                                # gather_r, init_sources, restart_loop, restore_r
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples taken while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        mx = [num(r[2]) for r in rows if num(r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def setup_dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(n: int, seed_cfg: str = "C4"):
+    """Time the single-heap FP64 oracle (one thread) on the workload family at n^3."""
+    import oracle
+    import synth
+    w = synth.workload(seed_cfg, n)
+    F = w.speed()
+    oracle.build()
+    t0 = time.perf_counter()
+    psi = oracle.fmm(F, w.h, w.sources)
+    dt = time.perf_counter() - t0
+    return w, F, psi, dt
+
+
+def run_reference(args):
+    ws, rank, _ = setup_dist()
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    n = args.ref_n
+    w = synth.workload("C4", n)
+    F = w.speed()
+    oracle.build()
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.fmm(F, w.h, w.sources)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = w.npoints * len(times) / total / 1e6
+    sample = (f"C4 family (same F recipe) at {n}^3, h=1/{n - 1}, centre source; single-heap FP64 fast "
+              f"marching oracle, one thread, one full solve per step")
+    line = {"metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"C4-family {n}^3 sample of the 1024^3 GRF workload (oracle)",
+                       "grid": [n, n, n]},
+            "cpu_baseline": {"value": value, "unit": "Mpoints/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = setup_dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    # CPU baseline first (rank 0, N = 1), before the GPU work starts
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        w_s, F_s, psi_s, dt = cpu_oracle_sample(args.cpu_n)
+        cpu = {"value": w_s.npoints / dt / 1e6, "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
+               "sample": f"one full solve of the C4 family at {args.cpu_n}^3 (same F recipe, h=1/{args.cpu_n - 1}, "
+                         f"centre source) by the single-heap FP64 fast marching oracle, one thread, {dt:.1f} s"}
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1811_00009_gb300 as eik
+    import synth
+
+    n = args.n
+    w = synth.workload("C4", n)
+    if rank:
+        w.seed += 1000 * rank                           # independent instance per rank
+    prec = args.precision
+    Fd = w.speed_torch(dev)
+    if prec == "fp64":
+        Fd = Fd.double()
+    ctx = eik.eik_create(w.dims, w.h, Fd, prec)
+    eik.eik_add_sources(ctx, w.sources)
+    stride = args.stride_h * w.h
+    kw = {"window": args.window} if args.window else {}
+
+    for _ in range(args.warmup):
+        st = eik.eik_solve_ex(ctx, stride, **kw)
+
+    stream = torch.cuda.current_stream()
+    pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    stats = []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t_start.record(stream)
+        for i in range(args.steps):
+            eik.eik_solve_async(ctx, stride, loop_events=pairs[i], **kw)
+            stats.append(eik.eik_wait(ctx))
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    loop_ms = [a.elapsed_time(b) for a, b in pairs]
+    if ws > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    total_points = w.npoints * args.steps * ws
+    value = total_points / (elapsed_ms * 1e-3) / 1e6
+
+    # roofline of the dominant kernel (the restart loop), algorithmic bytes per launch
+    peak, peak_kind = measured_peaks()
+    algo_bytes = ALGO_BYTES_PER_POINT[prec] * w.npoints
+    loop_avg_ms = sum(loop_ms) / len(loop_ms)
+    achieved = algo_bytes / (loop_avg_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_restart_loop", "peak_kind": peak_kind,
+            "algo_bytes_per_launch": algo_bytes, "launch_ms": loop_avg_ms}
+
+    # end to end through the public API with host buffers (pinned), per step:
+    # upload F, solve, read psi back
+    e2e = None
+    if not args.no_e2e:
+        Fh = torch.empty(Fd.shape, dtype=Fd.dtype, pin_memory=True)
+        Fh.copy_(Fd)
+        out_h = torch.empty(Fd.shape, dtype=Fd.dtype, pin_memory=True)
+        torch.cuda.synchronize()
+        eik.eik_set_speed(ctx, Fh.numpy(), prec)
+        eik.eik_solve_ex(ctx, stride, **kw)
+        eik.eik_result(ctx, out_h.numpy())
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            eik.eik_set_speed(ctx, Fh.numpy(), prec)
+            eik.eik_solve_ex(ctx, stride, **kw)
+            eik.eik_result(ctx, out_h.numpy())
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        nb = Fd.element_size() * w.npoints
+        e2e = {"value": w.npoints * args.e2e_steps * ws / e2e_s / 1e6, "unit": "Mpoints/s",
+               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb, "steps": args.e2e_steps}
+
+    # accuracy of this run's path against the FP64 oracle on the CPU-baseline sample
+    err = None
+    if cpu is not None:
+        Fs = torch.from_numpy(F_s.astype(np.float32 if prec == "fp32" else np.float64)).to(dev)
+        c2 = eik.eik_create(w_s.dims, w_s.h, Fs, prec)
+        eik.eik_add_sources(c2, w_s.sources)
+        eik.eik_solve_ex(c2, args.stride_h * w_s.h, **kw)
+        o = torch.empty_like(Fs)
+        eik.eik_result(c2, o)
+        eik.eik_destroy(c2)
+        p = o.double().cpu().numpy()
+        fin = np.isfinite(psi_s)
+        err = {"max_abs_over_max_psi": float(np.max(np.abs(p[fin] - psi_s[fin])) / psi_s[fin].max()),
+               "grid": [args.cpu_n] * 3, "tolerance": 1e-5 if prec == "fp32" else None}
+
+    eik.eik_destroy(ctx)
+    clocks = clk.summary()
+    s0 = stats[-1]
+    line = {"metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": (f"C4: {n}^3 node grid, h=1/{n - 1}, F=exp(g) random field std 0.5 corr 0.05, "
+                                    f"centre source, {prec.upper()} (FP64 root fallback), fixed stride "
+                                    f"{args.stride_h:g}h, 8^3 blocks"),
+                       "grid": [n, n, n], "stride_h": args.stride_h, "block": 8, "schedule": "fixed",
+                       "l2": "inputs larger than L2 (F and psi copies are GiB-sized), no flush",
+                       "parallelism": "independent solve per GPU" if ws > 1 else "single GPU"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": KERNELS_PER_SOLVE * args.steps, "clocks": clocks,
+            "solve": {"restarts": s0["restarts"], "marches": s0["marches"], "accepted": s0["accepted"],
+                      "solves": s0["solves"], "updates": s0["updates"], "fallbacks": s0["fallbacks"],
+                      "rounds": s0["rounds"], "loop_ms": loop_avg_ms},
+            "error_vs_oracle": err}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=1024, help="grid edge of the workload (default 1024)")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--stride-h", type=float, default=2.0)
+    ap.add_argument("--window", type=float, default=0.0)
+    ap.add_argument("--cpu-n", type=int, default=160)
+    ap.add_argument("--ref-n", type=int, default=128)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

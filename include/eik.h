@@ -1,0 +1,189 @@
+/*
+ * eik.h -- C ABI of the GB300 block-based restarted narrow-band fast marching
+ * solver (libeik.so).
+ *
+ * Problem (Sec. 1, Eq. (1.1)): |grad psi(x)| F(x) = 1 in the grid, psi = 0 on
+ * the point sources, F >= 0 (F = 0 marks a barrier node that is never solved,
+ * Sec. 3.3).  Discretisation (Sec. 2.1, Eqs. (2.1)-(2.2)): first-order Godunov
+ * upwind differences on a node-centred uniform grid of spacing h, node (i,j,k)
+ * at physical (i*h, j*h, k*h).  Method (Sec. 2.3-2.6, Alg. 6): the grid is cut
+ * into blocks; each restart raises a global bound by a stride, marches every
+ * active block's narrow band up to that bound (Alg. 4 with Algs. 2-3), and
+ * exchanges ghost layers between neighbouring blocks with a min-merge
+ * (Alg. 5), until no block is active.
+ *
+ * Conventions shared by every entry point:
+ *  - Arrays of grid values are nx*ny*nz elements, x fastest:
+ *    idx = (k*ny + j)*nx + i.  Element type follows the context precision:
+ *    float for EIK_FP32, double for EIK_FP64.
+ *  - "on_device" flags say whether a pointer is device memory (non-zero) or
+ *    host memory (zero).  The caller owns every buffer it passes; the library
+ *    copies what it keeps and never frees caller memory.
+ *  - The library owns all device memory it allocates; eik_destroy frees it.
+ *  - Every call is validated.  Errors are return codes, never exceptions or
+ *    aborts; eik_last_error() describes the most recent failure.
+ *  - Work is issued on the stream given to eik_create (NULL = the legacy
+ *    default stream).  eik_solve and eik_result return after that work has
+ *    finished; eik_solve_async returns after queueing it.
+ *  - One context is used by one host thread at a time.
+ */
+#ifndef EIK_H
+#define EIK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct eik_ctx eik_ctx;
+
+typedef enum {
+    EIK_OK = 0,
+    EIK_EINVAL = 1,    /* invalid argument (dims, h, F, sources, parameters) */
+    EIK_ENOMEM = 2,    /* a device or host allocation failed */
+    EIK_ECUDA = 3,     /* a CUDA call failed (eik_last_error has the CUDA message) */
+    EIK_ETIMEOUT = 4,  /* the restart cap was reached or a device wait ran out of iterations */
+    EIK_ESTATE = 5,    /* call out of order: e.g. eik_solve before any source */
+    EIK_ENOTSUP = 6    /* valid request this build does not support */
+} eik_status;
+
+typedef enum { EIK_FP32 = 0, EIK_FP64 = 1 } eik_precision;
+
+/*
+ * eik_create -- build a solver context for one grid and speed function.
+ *   out          receives the context (set to NULL on failure).
+ *   dims         nx, ny, nz >= 1 (grid nodes per axis); nx*ny*nz < 2^31.
+ *   h            grid spacing, finite and > 0.
+ *   F            nx*ny*nz speeds (float for EIK_FP32, double for EIK_FP64),
+ *                each finite and >= 0.  Copied; the caller keeps its buffer.
+ *   F_on_device  non-zero if F is device memory.
+ *   precision    EIK_FP32: psi and F stored and updated in single precision
+ *                (the upwind root falls back to double, Alg. 3, when its
+ *                discriminant is small relative to k*(h/F)^2 or (h/F)^2
+ *                underflows); EIK_FP64: everything in double.
+ *   stream       a cudaStream_t, or NULL.
+ * Errors: EIK_EINVAL (bad dims/h, F < 0, NaN or inf), EIK_ENOMEM, EIK_ECUDA.
+ */
+eik_status eik_create(eik_ctx **out, const int32_t dims[3], double h, const void *F,
+                      int F_on_device, eik_precision precision, void *stream);
+
+/*
+ * eik_set_speed -- replace the speed function of an existing context (same
+ * grid, h and precision); F as in eik_create.  Sources are kept.
+ * Errors: EIK_EINVAL (NULL F, F < 0, NaN or inf; the old speeds are then
+ * undefined until a successful call), EIK_ESTATE (a solve is in flight).
+ */
+eik_status eik_set_speed(eik_ctx *ctx, const void *F, int F_on_device);
+
+/*
+ * eik_add_sources -- add point sources (Gamma of Eq. (1.1)).
+ *   xyz  n*3 physical coordinates (x, y, z), origin at node 0, each within
+ *        [0, (n_axis - 1)*h].  The nodes of the grid cell containing a source
+ *        (one node if it lies on a node, 2/4 on an edge/face, 8 inside) become
+ *        fixed with psi0 = distance / F there (Alg. 1, "on or adjacent to
+ *        Gamma"); a node reached by several sources keeps the smallest psi0.
+ * Errors: EIK_EINVAL (n < 0, a coordinate outside the grid box or not finite).
+ */
+eik_status eik_add_sources(eik_ctx *ctx, int32_t n, const double *xyz);
+
+/* eik_clear_sources -- forget every source added so far. */
+eik_status eik_clear_sources(eik_ctx *ctx);
+
+/* Schedules of the restart bound (Alg. 6: bound <- min(bound + stride, width)). */
+typedef enum {
+    EIK_SCHED_FIXED = 0,   /* every restart advances the bound by `stride` */
+    EIK_SCHED_LEARNED = 1  /* a trained network picks the stride per restart (eik_sched_load) */
+} eik_schedule;
+
+typedef struct {
+    double stride;          /* bound increment in psi units (> 0; +inf = the naive block method) */
+    int32_t block_dim;      /* block edge in nodes: 8 (0 = default 8) */
+    int32_t schedule;       /* eik_schedule */
+    double window;          /* acceptance window factor omega: each march round accepts every band
+                               point within omega * h / F_max(block) of the band minimum
+                               (0 = default 1/sqrt(3)) */
+    double fallback_tau;    /* FP32 mode: fall back to double when D < tau * k * (h/F)^2 (0 = default 1/8) */
+    int64_t max_restarts;   /* restart cap (0 = default 1 << 24); reaching it returns EIK_ETIMEOUT */
+    int32_t log_restarts;   /* non-zero: record per-restart statistics (eik_restart_log) */
+    int32_t reserved;
+    void *loop_events[2];   /* optional cudaEvent_t pair the library records on its stream right
+                               before and right after the restart-loop kernel (NULL: none) */
+} eik_params;
+
+/* Per-solve statistics, filled by eik_solve / eik_wait. */
+typedef struct {
+    int64_t restarts;       /* nr: iterations of the restart loop of Alg. 6 */
+    int64_t marches;        /* block marches (active or flagged blocks, summed over restarts) */
+    int64_t accepted;       /* band points accepted (heap pops in Alg. 4), refreshes included */
+    int64_t solves;         /* upwind solves (Alg. 3 calls) */
+    int64_t updates;        /* solves that lowered psi (Alg. 2 accepted updates) */
+    int64_t fallbacks;      /* FP32 roots recomputed in double */
+    int64_t rounds;         /* acceptance rounds over all marches */
+    double device_ms;       /* device time of the restart loop (%globaltimer) */
+    double final_bound;     /* bound of the last restart */
+    int32_t status;         /* eik_status of the device run */
+    int32_t block_dim;      /* block edge used */
+} eik_stats;
+
+/* One record per restart when eik_params.log_restarts is set. */
+typedef struct {
+    int32_t k;              /* restart index, 1-based */
+    int32_t active;         /* blocks marched in this restart */
+    int64_t band;           /* band points left (pending) at the end of the restart */
+    int64_t accepted;       /* points accepted in this restart */
+    double bound;           /* bound_band of this restart */
+    double stride;          /* stride that produced this bound */
+    double rmin;            /* min h/F over the marched blocks */
+    double rmax;            /* max h/F over the marched blocks */
+    double ms;              /* device time of the restart */
+} eik_restart_rec;
+
+/* eik_params_default -- fill *p with the defaults above and stride = 2h-equivalent 0 (caller sets stride). */
+void eik_params_default(eik_params *p);
+
+/*
+ * eik_solve -- run the method (Alg. 6) with a fixed stride and wait for it.
+ *   stride     > 0, may be +inf.
+ *   block_dim  8, or 0 for the default.
+ *   stats      nullable.
+ * Returns EIK_ESTATE if no source was added, EIK_ETIMEOUT if the restart cap
+ * or a device wait limit was hit.
+ */
+eik_status eik_solve(eik_ctx *ctx, double stride, int32_t block_dim, eik_stats *stats);
+
+/* eik_solve_ex -- eik_solve with every parameter; waits for completion. */
+eik_status eik_solve_ex(eik_ctx *ctx, const eik_params *params, eik_stats *stats);
+
+/* eik_solve_async -- queue the solve on the context's stream and return;
+ * eik_wait then synchronises and reports. */
+eik_status eik_solve_async(eik_ctx *ctx, const eik_params *params);
+eik_status eik_wait(eik_ctx *ctx, eik_stats *stats);
+
+/*
+ * eik_restart_log -- copy up to cap per-restart records of the last solve
+ * (made with log_restarts set) into out (host memory); *n gets the count.
+ */
+eik_status eik_restart_log(eik_ctx *ctx, eik_restart_rec *out, int64_t cap, int64_t *n);
+
+/*
+ * eik_result -- copy psi of the last solve into psi_out (nx*ny*nz, context
+ * precision, x fastest).  Unreachable nodes and barrier nodes are +inf.
+ * Errors: EIK_ESTATE before the first successful solve.
+ */
+eik_status eik_result(eik_ctx *ctx, void *psi_out, int out_on_device);
+
+/* eik_destroy -- free the context and everything it allocated (NULL is a no-op). */
+void eik_destroy(eik_ctx *ctx);
+
+/* eik_last_error -- message of the last failure on ctx (or of the last failed
+ * eik_create when ctx is NULL).  Valid until the next call on ctx. */
+const char *eik_last_error(const eik_ctx *ctx);
+
+/* eik_version -- library version string. */
+const char *eik_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

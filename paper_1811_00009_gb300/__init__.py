@@ -1,0 +1,303 @@
+"""Python binding of libeik, the GB300 block-based restarted narrow-band fast marching solver.
+
+Argument marshalling only: every step of the solve runs in the CUDA kernels
+behind the C ABI of include/eik.h.  Device buffers are torch CUDA tensors
+(passed by data_ptr, on torch's current stream); host buffers are numpy arrays.
+There is no CPU fallback: if libeik.so is missing or cannot be loaded, every
+call raises.
+
+    ctx = eik_create((nx, ny, nz), h, F, precision="fp32")
+    eik_add_sources(ctx, [[x, y, z], ...])
+    stats = eik_solve(ctx, stride=2 * h)
+    psi = eik_result(ctx, out)          # out: torch CUDA tensor or numpy array, shape (nz, ny, nx)
+    eik_destroy(ctx)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+from typing import Any, Dict, List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libeik.so")
+
+EIK_OK, EIK_EINVAL, EIK_ENOMEM, EIK_ECUDA, EIK_ETIMEOUT, EIK_ESTATE, EIK_ENOTSUP = range(7)
+EIK_FP32, EIK_FP64 = 0, 1
+EIK_SCHED_FIXED, EIK_SCHED_LEARNED = 0, 1
+STATUS_NAMES = {0: "EIK_OK", 1: "EIK_EINVAL", 2: "EIK_ENOMEM", 3: "EIK_ECUDA", 4: "EIK_ETIMEOUT",
+                5: "EIK_ESTATE", 6: "EIK_ENOTSUP"}
+
+
+class EikError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class eik_params(C.Structure):
+    _fields_ = [("stride", C.c_double), ("block_dim", C.c_int32), ("schedule", C.c_int32),
+                ("window", C.c_double), ("fallback_tau", C.c_double), ("max_restarts", C.c_int64),
+                ("log_restarts", C.c_int32), ("reserved", C.c_int32), ("loop_events", C.c_void_p * 2)]
+
+
+class eik_stats(C.Structure):
+    _fields_ = [("restarts", C.c_int64), ("marches", C.c_int64), ("accepted", C.c_int64),
+                ("solves", C.c_int64), ("updates", C.c_int64), ("fallbacks", C.c_int64),
+                ("rounds", C.c_int64), ("device_ms", C.c_double), ("final_bound", C.c_double),
+                ("status", C.c_int32), ("block_dim", C.c_int32)]
+
+
+class eik_restart_rec(C.Structure):
+    _fields_ = [("k", C.c_int32), ("active", C.c_int32), ("band", C.c_int64), ("accepted", C.c_int64),
+                ("bound", C.c_double), ("stride", C.c_double), ("rmin", C.c_double), ("rmax", C.c_double),
+                ("ms", C.c_double)]
+
+
+_lock = threading.Lock()
+_L = None
+
+
+def lib():
+    """Load libeik.so (built by build.py / __graft_entry__.build()).  Raises if absent."""
+    global _L
+    with _lock:
+        if _L is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"libeik.so not found at {LIB_PATH}: build it with "
+                                  "python -c 'import __graft_entry__ as g; g.build()'")
+            L = C.CDLL(LIB_PATH)
+            vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+            L.eik_create.restype = i32
+            L.eik_create.argtypes = [C.POINTER(vp), C.POINTER(i32), dbl, vp, C.c_int, C.c_int, vp]
+            L.eik_set_speed.restype = i32
+            L.eik_set_speed.argtypes = [vp, vp, C.c_int]
+            L.eik_add_sources.restype = i32
+            L.eik_add_sources.argtypes = [vp, i32, C.POINTER(dbl)]
+            L.eik_clear_sources.restype = i32
+            L.eik_clear_sources.argtypes = [vp]
+            L.eik_params_default.restype = None
+            L.eik_params_default.argtypes = [C.POINTER(eik_params)]
+            L.eik_solve.restype = i32
+            L.eik_solve.argtypes = [vp, dbl, i32, C.POINTER(eik_stats)]
+            L.eik_solve_ex.restype = i32
+            L.eik_solve_ex.argtypes = [vp, C.POINTER(eik_params), C.POINTER(eik_stats)]
+            L.eik_solve_async.restype = i32
+            L.eik_solve_async.argtypes = [vp, C.POINTER(eik_params)]
+            L.eik_wait.restype = i32
+            L.eik_wait.argtypes = [vp, C.POINTER(eik_stats)]
+            L.eik_restart_log.restype = i32
+            L.eik_restart_log.argtypes = [vp, C.POINTER(eik_restart_rec), i64, C.POINTER(i64)]
+            L.eik_result.restype = i32
+            L.eik_result.argtypes = [vp, vp, C.c_int]
+            L.eik_destroy.restype = None
+            L.eik_destroy.argtypes = [vp]
+            L.eik_last_error.restype = C.c_char_p
+            L.eik_last_error.argtypes = [vp]
+            L.eik_version.restype = C.c_char_p
+            L.eik_version.argtypes = []
+            _L = L
+    return _L
+
+
+def eik_last_error(ctx=None) -> str:
+    m = lib().eik_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def _check(status: int, ctx=None):
+    if status != EIK_OK:
+        raise EikError(status, eik_last_error(ctx))
+
+
+def _precision(p) -> int:
+    if p in ("fp32", EIK_FP32, "float32"):
+        return EIK_FP32
+    if p in ("fp64", EIK_FP64, "float64"):
+        return EIK_FP64
+    raise ValueError(f"precision {p!r}")
+
+
+def _buffer(a, want_dtype):
+    """(pointer, on_device, keepalive) for a torch tensor or numpy array of the given element type."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            tdt = torch.float32 if want_dtype == np.float32 else torch.float64
+            if a.dtype != tdt or not a.is_contiguous():
+                raise ValueError(f"tensor must be contiguous {tdt}")
+            return C.c_void_p(a.data_ptr()), int(a.is_cuda), a
+    except ImportError:
+        pass
+    arr = np.asarray(a)
+    if arr.dtype != want_dtype or not arr.flags.c_contiguous:
+        raise ValueError(f"array must be C-contiguous {np.dtype(want_dtype).name}")
+    return C.c_void_p(arr.ctypes.data), 0, arr
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return C.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def eik_create(dims: Sequence[int], h: float, F, precision="fp32", stream=None):
+    """Context for grid dims=(nx, ny, nz), spacing h, speeds F (shape (nz, ny, nx), x fastest)."""
+    prec = _precision(precision)
+    ptr, on_dev, keep = _buffer(F, np.float32 if prec == EIK_FP32 else np.float64)
+    n = int(dims[0]) * int(dims[1]) * int(dims[2])
+    if int(np.prod(getattr(keep, "shape", (0,)))) != n:
+        raise ValueError("F must hold nx*ny*nz values")
+    d = (C.c_int32 * 3)(*[int(x) for x in dims])
+    out = C.c_void_p()
+    _check(lib().eik_create(C.byref(out), d, float(h), ptr, on_dev, prec, _stream_handle(stream)), None)
+    return out
+
+
+def eik_set_speed(ctx, F, precision="fp32") -> None:
+    """Replace the context's speed function (same grid and precision)."""
+    ptr, on_dev, keep = _buffer(F, np.float32 if _precision(precision) == EIK_FP32 else np.float64)
+    _check(lib().eik_set_speed(ctx, ptr, on_dev), ctx)
+
+
+def eik_add_sources(ctx, xyz) -> None:
+    a = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
+    _check(lib().eik_add_sources(ctx, len(a), a.ctypes.data_as(C.POINTER(C.c_double))), ctx)
+
+
+def eik_clear_sources(ctx) -> None:
+    _check(lib().eik_clear_sources(ctx), ctx)
+
+
+def eik_params_default() -> eik_params:
+    p = eik_params()
+    lib().eik_params_default(C.byref(p))
+    return p
+
+
+def _stats_dict(s: eik_stats) -> Dict[str, Any]:
+    return {k: getattr(s, k) for k, _ in eik_stats._fields_}
+
+
+def _params(stride: float, **kw) -> eik_params:
+    p = eik_params_default()
+    p.stride = float(stride)
+    for k, v in kw.items():
+        if k == "loop_events":
+            p.loop_events[0] = C.c_void_p(v[0].cuda_event if hasattr(v[0], "cuda_event") else int(v[0]))
+            p.loop_events[1] = C.c_void_p(v[1].cuda_event if hasattr(v[1], "cuda_event") else int(v[1]))
+            continue
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+def eik_solve(ctx, stride: float, block_dim: int = 8) -> Dict[str, Any]:
+    s = eik_stats()
+    _check(lib().eik_solve(ctx, float(stride), int(block_dim), C.byref(s)), ctx)
+    return _stats_dict(s)
+
+
+def eik_solve_ex(ctx, stride: float, **kw) -> Dict[str, Any]:
+    p = _params(stride, **kw)
+    s = eik_stats()
+    _check(lib().eik_solve_ex(ctx, C.byref(p), C.byref(s)), ctx)
+    return _stats_dict(s)
+
+
+def eik_solve_async(ctx, stride: float, **kw) -> None:
+    p = _params(stride, **kw)
+    _check(lib().eik_solve_async(ctx, C.byref(p)), ctx)
+
+
+def eik_wait(ctx) -> Dict[str, Any]:
+    s = eik_stats()
+    _check(lib().eik_wait(ctx, C.byref(s)), ctx)
+    return _stats_dict(s)
+
+
+def eik_restart_log(ctx, cap: int = 1 << 16) -> List[Dict[str, Any]]:
+    recs = (eik_restart_rec * cap)()
+    n = C.c_int64()
+    _check(lib().eik_restart_log(ctx, recs, cap, C.byref(n)), ctx)
+    return [{k: getattr(recs[i], k) for k, _ in eik_restart_rec._fields_} for i in range(n.value)]
+
+
+def eik_result(ctx, out):
+    """Write psi into `out` (torch CUDA tensor or numpy array, context precision) and return it."""
+    for dt in (np.float32, np.float64):
+        try:
+            ptr, on_dev, keep = _buffer(out, dt)
+            break
+        except ValueError:
+            continue
+    else:
+        raise ValueError("out must be a contiguous float32/float64 tensor or array")
+    _check(lib().eik_result(ctx, ptr, on_dev), ctx)
+    return out
+
+
+def eik_destroy(ctx) -> None:
+    if ctx:
+        lib().eik_destroy(ctx)
+
+
+def eik_version() -> str:
+    return lib().eik_version().decode()
+
+
+class Solver:
+    """Owns one context; convenience wrapper over the functions above."""
+
+    def __init__(self, dims, h, F, precision="fp32", stream=None):
+        self.dims = tuple(int(x) for x in dims)
+        self.h = float(h)
+        self.precision = precision
+        self.ctx = eik_create(self.dims, h, F, precision, stream)
+
+    def add_sources(self, xyz):
+        eik_add_sources(self.ctx, xyz)
+
+    def clear_sources(self):
+        eik_clear_sources(self.ctx)
+
+    def solve(self, stride: float, **kw):
+        return eik_solve_ex(self.ctx, stride, **kw)
+
+    def result(self, out=None):
+        if out is None:
+            dt = np.float32 if _precision(self.precision) == EIK_FP32 else np.float64
+            out = np.empty(self.dims[::-1], dtype=dt)
+        return eik_result(self.ctx, out)
+
+    def restart_log(self):
+        return eik_restart_log(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            eik_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

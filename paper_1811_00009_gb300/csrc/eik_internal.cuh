@@ -1,0 +1,100 @@
+// Internal definitions of libeik (not part of the C ABI).
+//
+// Data layout in HBM (one grid):
+//   bricks of 8x8x8 nodes, brick b = (bz*BY + by)*BX + bx, node p = (z*8 + y)*8 + x
+//   inside a brick; a ragged last brick per axis is padded with barrier nodes.
+//   rr[b][512]          h/F (+inf: barrier or padding, -1: fixed source node)
+//   slot[b][2][640]     two copies of the brick's psi: 512 interior values,
+//                       then its x = 0 and x = 7 faces (64 each, index z*8+y)
+//                       stored contiguously for the neighbours' ghost reads
+//   slot_k[b][2]        restart that wrote each copy (-1: never)
+//   ups[b][2][6]        per copy, the 64-bit mask of face nodes lowered in the
+//                       march that wrote it (Upsilon of Alg. 2/4), per face
+//   stamp[b]            (restart << 1) | copy of the latest state, -1 untouched
+//   queued[b]           last restart the brick was put on the work list for
+// A march at restart k reads the brick's latest copy and its neighbours' copies
+// as of the end of restart k-1, and writes the other copy, so no warp ever
+// reads memory written during the same restart: the exchange step of Alg. 5
+// needs no second grid-wide barrier.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace eikg {
+
+constexpr int kEdge = 8;           // brick edge (nodes)
+constexpr int kBrick = 512;        // nodes per brick
+constexpr int kSlot = 640;         // values per brick copy
+constexpr int kXF0 = 512;          // offset of the x = 0 face inside a copy
+constexpr int kXF7 = 576;          // offset of the x = 7 face
+constexpr int kWarps = 8;          // warps per CTA of the restart loop (one brick per warp)
+
+// status bits of a device run
+constexpr int kStWaitTimeout = 1;  // a grid-barrier wait ran out of iterations
+constexpr int kStRestartCap = 2;   // max_restarts reached with work left
+constexpr int kStRoundCap = 4;     // a march exceeded its round cap
+
+// Control block of one restart loop, in device memory.  Written by the CTA
+// that arrives last at each grid barrier, read by all after the release.
+struct Ctrl {
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    int32_t k;                 // current restart (1-based)
+    int32_t done;
+    int32_t status;
+    int32_t count[2];          // work-list lengths, by restart parity
+    int32_t head[2];           // next work-list entry to hand out
+    int32_t pad0;
+    double bound;              // bound_band of restart k
+    double bound_prev;         // bound_band of restart k-1 (-1 at k = 1)
+    double stride;             // stride that produced `bound`
+    unsigned long long t_begin;
+    unsigned long long t_restart;
+    unsigned long long t_end;
+    // accumulators of the current restart
+    unsigned long long r_accepted, r_band, r_solves, r_updates, r_fallbacks, r_rounds;
+    unsigned int r_rmin_bits, r_rmax_bits;
+    // totals
+    unsigned long long marches, accepted, solves, updates, fallbacks, rounds;
+};
+
+struct RestartRec {            // mirrors eik_restart_rec
+    int32_t k;
+    int32_t active;
+    int64_t band;
+    int64_t accepted;
+    double bound;
+    double stride;
+    double rmin;
+    double rmax;
+    double ms;
+};
+
+template <typename T>
+struct LoopParams {
+    int32_t nx, ny, nz;
+    int32_t BX, BY, BZ;
+    int64_t nbricks;
+    T* slot;
+    int32_t* slot_k;
+    unsigned long long* ups;
+    int32_t* stamp;
+    int32_t* queued;
+    const T* rr;
+    int32_t* list0;
+    int32_t* list1;
+    Ctrl* ctrl;
+    RestartRec* log;
+    int64_t log_cap;
+    double window;             // omega: acceptance window = omega * min(h/F) over the brick
+    double fallback_tau;       // FP32: double-precision root when D < tau * k * r^2
+    int64_t max_restarts;
+    long long wait_limit;      // spin iterations before a barrier wait gives up
+    int32_t sched;             // 0 fixed, 1 learned
+    int32_t pad;
+    const float* mlp;          // schedule network weights (learned schedule)
+    double h;
+};
+
+}  // namespace eikg

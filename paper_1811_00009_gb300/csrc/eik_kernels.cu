@@ -1,0 +1,909 @@
+// Device kernels of libeik: the block-based restarted narrow-band fast
+// marching method (J. Yang 2018, Alg. 6 with Algs. 1-5) on sm_103a.
+//
+// One warp marches one 8x8x8 block (a "brick").  The brick's psi, h/F and its
+// six ghost faces sit in shared memory; lane L owns the two x-rows
+// (y = L & 7, z = 2*(L >> 3) + {0, 1}) as a 16-bit mask, plus the ghost nodes
+// next to them.  The band (Sec. 2.1 BAND set) is a per-lane bit mask; a band
+// node's value carries its sign bit set in shared memory so that any lane can
+// tell a tentative value from an accepted (KNOWN) one with one load.
+//
+// Ordered extraction (Alg. 4) is done in rounds: each round takes the band
+// minimum m with a warp reduction and accepts every band node with
+// psi <= min(m + w, bound), w = omega * min(h/F) over the brick; the
+// neighbours of the accepted nodes (Alg. 2) are compacted into a list and
+// re-solved (Alg. 3) 32 at a time.  A lowered node rejoins the band, so an
+// accepted node can be refreshed later exactly as a KNOWN_NEW node of the
+// paper can.  With w = 0 this is the paper's one-node-at-a-time order.
+//
+// The restart loop of Alg. 6 runs in one cooperative persistent kernel with
+// one grid-wide barrier per restart; the exchange step (Alg. 5) is fused into
+// the start of the next march (see eik_internal.cuh for the double-copy
+// layout that makes this race-free, the argument of Sec. 2.7).
+#include "eik_internal.cuh"
+
+#include <cfloat>
+#include <cstdint>
+
+namespace eikg {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kRoundCap = 1 << 20;
+
+template <typename T>
+struct Num;
+template <>
+struct Num<float> {
+    static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+};
+template <>
+struct Num<double> {
+    static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000LL); }
+};
+
+__device__ __forceinline__ bool sgn(float v) { return (__float_as_uint(v) >> 31) != 0u; }
+__device__ __forceinline__ bool sgn(double v) {
+    return (static_cast<unsigned long long>(__double_as_longlong(v)) >> 63) != 0ull;
+}
+__device__ __forceinline__ float vabs(float v) { return fabsf(v); }
+__device__ __forceinline__ double vabs(double v) { return fabs(v); }
+__device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 3: the upwind root for sorted upwind values a <= b <= c (b, c may be
+// +inf) and r = h/F.  Alg. 3 solves a x^2 - 2 b x + c = 0 for the id
+// smallest values, growing id while the root exceeds the next value.  Here
+// the same root is written without cancellation: with k admitted values,
+//   x = v_1 + (sum_i (v_i - v_1) + sqrt(D)) / k,
+//   D = k r^2 - sum_{i<j} (v_i - v_j)^2          (Lagrange's identity),
+// whose differences are exact.  Whenever a value is admitted D > r^2 in
+// exact arithmetic, so D < tau*k*r^2 (tau < 1/3) only flags rounding trouble.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double upwind_root(double a, double b, double c, double r) {
+    double x = a + r;
+    if (!(x > b)) return x;
+    const double d = b - a;
+    const double r2 = r * r;
+    double D = 2.0 * r2 - d * d;
+    x = a + (d + sqrt(fmax(D, 0.0))) * 0.5;
+    if (!(x > c)) return x;
+    const double e = c - a, g = c - b;
+    D = 3.0 * r2 - (d * d + e * e + g * g);
+    return a + (d + e + sqrt(fmax(D, 0.0))) / 3.0;
+}
+
+__device__ __forceinline__ float upwind_root_f32(float a, float b, float c, float r, float tau, int& fb) {
+    float x = a + r;
+    if (!(x > b)) return x;
+    const float d = b - a;
+    const float r2 = r * r;
+    float D = 2.0f * r2 - d * d;
+    if (!(r2 >= FLT_MIN) || !(D >= tau * 2.0f * r2)) {
+        ++fb;
+        return static_cast<float>(upwind_root(a, b, c, r));
+    }
+    x = a + (d + sqrtf(D)) * 0.5f;
+    if (!(x > c)) return x;
+    const float e = c - a, g = c - b;
+    D = 3.0f * r2 - (d * d + e * e + g * g);
+    if (!(D >= tau * 3.0f * r2)) {
+        ++fb;
+        return static_cast<float>(upwind_root(a, b, c, r));
+    }
+    return a + (d + e + sqrtf(D)) / 3.0f;
+}
+
+template <typename T>
+struct RootOf;
+template <>
+struct RootOf<float> {
+    static __device__ __forceinline__ float go(float a, float b, float c, float r, float tau, int& fb) {
+        return upwind_root_f32(a, b, c, r, tau, fb);
+    }
+};
+template <>
+struct RootOf<double> {
+    static __device__ __forceinline__ double go(double a, double b, double c, double r, float, int&) {
+        return upwind_root(a, b, c, r);
+    }
+};
+
+// Per-warp shared memory.
+template <typename T>
+struct __align__(16) WarpSmem {
+    T psi[1000];          // brick plus one ghost layer, index ((z+1)*10 + (y+1))*10 + (x+1)
+    T r[kBrick];          // h/F, brick index
+    uint16_t list[kBrick];
+    uint8_t newp[kBrick]; // nodes lowered in the current round (byte flags)
+};
+
+__device__ __forceinline__ int halo_of(int p) {
+    const int x = p & 7, y = (p >> 3) & 7, z = p >> 6;
+    return ((z + 1) * 10 + (y + 1)) * 10 + (x + 1);
+}
+
+template <typename T>
+__device__ __forceinline__ void load8_cg(const T* g, T* out);
+template <>
+__device__ __forceinline__ void load8_cg<float>(const float* g, float* out) {
+    const float4 a = __ldcg(reinterpret_cast<const float4*>(g));
+    const float4 b = __ldcg(reinterpret_cast<const float4*>(g) + 1);
+    out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+    out[4] = b.x; out[5] = b.y; out[6] = b.z; out[7] = b.w;
+}
+template <>
+__device__ __forceinline__ void load8_cg<double>(const double* g, double* out) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const double2 a = __ldcg(reinterpret_cast<const double2*>(g) + i);
+        out[2 * i] = a.x;
+        out[2 * i + 1] = a.y;
+    }
+}
+template <typename T>
+__device__ __forceinline__ void load8_ro(const T* g, T* out);
+template <>
+__device__ __forceinline__ void load8_ro<float>(const float* g, float* out) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(g));
+    const float4 b = __ldg(reinterpret_cast<const float4*>(g) + 1);
+    out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+    out[4] = b.x; out[5] = b.y; out[6] = b.z; out[7] = b.w;
+}
+template <>
+__device__ __forceinline__ void load8_ro<double>(const double* g, double* out) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(g) + i);
+        out[2 * i] = a.x;
+        out[2 * i + 1] = a.y;
+    }
+}
+template <typename T>
+__device__ __forceinline__ void store8(T* g, const T* v);
+template <>
+__device__ __forceinline__ void store8<float>(float* g, const float* v) {
+    reinterpret_cast<float4*>(g)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4*>(g)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+template <>
+__device__ __forceinline__ void store8<double>(double* g, const double* v) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) reinterpret_cast<double2*>(g)[i] = make_double2(v[2 * i], v[2 * i + 1]);
+}
+template <typename T>
+__device__ __forceinline__ void load2_cg(const T* g, T& a, T& b);
+template <>
+__device__ __forceinline__ void load2_cg<float>(const float* g, float& a, float& b) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(g));
+    a = v.x;
+    b = v.y;
+}
+template <>
+__device__ __forceinline__ void load2_cg<double>(const double* g, double& a, double& b) {
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(g));
+    a = v.x;
+    b = v.y;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_min(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = vmin(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = vmax(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_or64(unsigned long long v) {
+    const unsigned lo = __reduce_or_sync(kFull, static_cast<unsigned>(v));
+    const unsigned hi = __reduce_or_sync(kFull, static_cast<unsigned>(v >> 32));
+    return (static_cast<unsigned long long>(hi) << 32) | lo;
+}
+// eight 0/1 bytes -> eight bits (byte i -> bit i)
+__device__ __forceinline__ unsigned pack_bytes(unsigned long long x) {
+    return static_cast<unsigned>((x * 0x0102040810204080ull) >> 56);
+}
+
+struct MarchAcc {
+    unsigned accepted, band;                 // per lane
+    int fallbacks;                           // per lane
+    unsigned long long solves, updates, rounds;  // the same on every lane
+    float rmin, rmax;                        // the same on every lane
+};
+
+// Halo index of ghost bit `bit` owned by this lane (see the G layout below).
+__device__ __forceinline__ int ghost_halo(int bit, int y, int z0) {
+    if (bit < 4) {
+        const int z = z0 + (bit & 1);
+        const int x = (bit & 2) ? 9 : 0;                 // x = -1 or x = 8
+        return ((z + 1) * 10 + (y + 1)) * 10 + x;
+    }
+    if (bit < 20) {
+        const int j = bit - 4, x = j & 7, z = z0 + (j >> 3);
+        const int row = (y == 0) ? 0 : 9;                // y = -1 or y = 8
+        return ((z + 1) * 10 + row) * 10 + (x + 1);
+    }
+    const int x = bit - 20;
+    const int plane = (z0 == 0) ? 0 : 9;                 // z = -1 or z = 8
+    return (plane * 10 + (y + 1)) * 10 + (x + 1);
+}
+
+// March_Narrow_Band (Alg. 4) of brick b at restart k, with the exchange of
+// Alg. 5 for its ghost layer done first from the neighbours' copies as of
+// the end of restart k-1.
+template <typename T>
+__device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, int k, double bprev,
+                            double bound, int lane, MarchAcc& acc) {
+    const T INF = Num<T>::inf();
+    const int y = lane & 7, zp = lane >> 3, z0 = 2 * zp;
+    const int BX = P.BX, BY = P.BY, BZ = P.BZ;
+    const int bx = b % BX, by = (b / BX) % BY, bz = b / (BX * BY);
+    const int pbase = (z0 * 8 + y) * 8;                          // brick index of (0, y, z0)
+    const int hbase = ((z0 + 1) * 10 + (y + 1)) * 10 + 1;       // halo index of (0, y, z0)
+
+    // ---- own state: the latest copy, or +inf for an untouched brick
+    const int32_t st = __ldcg(P.stamp + b);
+    {
+        T row[8];
+        if (st < 0) {
+#pragma unroll
+            for (int x = 0; x < 8; ++x) S.psi[hbase + x] = INF, S.psi[hbase + 100 + x] = INF;
+        } else {
+            const T* src = P.slot + (static_cast<int64_t>(b) * 2 + (st & 1)) * kSlot;
+            load8_cg(src + pbase, row);
+#pragma unroll
+            for (int x = 0; x < 8; ++x) S.psi[hbase + x] = row[x];
+            load8_cg(src + pbase + 64, row);
+#pragma unroll
+            for (int x = 0; x < 8; ++x) S.psi[hbase + 100 + x] = row[x];
+        }
+    }
+    // ---- h/F: fixed nodes (r < 0) and barrier/padding nodes (r = +inf) are never solved
+    unsigned FXOB = 0;
+    T rlo = INF, rhi = 0;
+    {
+        T row[8];
+        const T* rs = P.rr + static_cast<int64_t>(b) * kBrick;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            load8_ro(rs + pbase + 64 * s, row);
+            store8(S.r + pbase + 64 * s, row);
+#pragma unroll
+            for (int x = 0; x < 8; ++x) {
+                const T r = row[x];
+                if (!(r > 0) || !(r < INF)) FXOB |= 1u << (8 * s + x);
+                else {
+                    rlo = vmin(rlo, r);
+                    rhi = vmax(rhi, r);
+                }
+            }
+        }
+    }
+    // ---- ghost layer: neighbours' faces as of the end of restart k-1 (Alg. 5)
+    int nbr[6];
+    nbr[0] = bx > 0 ? b - 1 : -1;
+    nbr[1] = bx < BX - 1 ? b + 1 : -1;
+    nbr[2] = by > 0 ? b - BX : -1;
+    nbr[3] = by < BY - 1 ? b + BX : -1;
+    nbr[4] = bz > 0 ? b - BX * BY : -1;
+    nbr[5] = bz < BZ - 1 ? b + BX * BY : -1;
+    unsigned long long fups[6];
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        const int nb = nbr[f];
+        int sl = -1;
+        unsigned long long um = 0;
+        if (nb >= 0) {
+            const int32_t w = __ldcg(P.stamp + nb);
+            if (w >= 0) {
+                sl = w & 1;
+                int32_t written = w >> 1;
+                if (written >= k) {                               // already marched in this restart
+                    sl ^= 1;
+                    written = __ldcg(P.slot_k + 2 * nb + sl);
+                    if (written < 0) sl = -1;
+                }
+                if (sl >= 0 && written == k - 1)
+                    um = __ldcg(P.ups + (static_cast<int64_t>(nb) * 2 + sl) * 6 + (f ^ 1));
+            }
+        }
+        fups[f] = um;
+        const int u = 2 * lane;                                   // face-local index of this lane's pair
+        T v0 = INF, v1 = INF;
+        if (sl >= 0) {
+            const T* src = P.slot + (static_cast<int64_t>(nb) * 2 + sl) * kSlot;
+            int off;
+            if (f == 0) off = kXF7 + u;
+            else if (f == 1) off = kXF0 + u;
+            else if (f == 2) off = ((u >> 3) * 8 + 7) * 8 + (u & 7);
+            else if (f == 3) off = ((u >> 3) * 8 + 0) * 8 + (u & 7);
+            else if (f == 4) off = 7 * 64 + u;
+            else off = u;
+            load2_cg(src + off, v0, v1);
+        }
+        int h0, step;
+        if (f < 2) {
+            const int yy = u & 7, zz = u >> 3;
+            h0 = ((zz + 1) * 10 + (yy + 1)) * 10 + (f == 0 ? 0 : 9);
+            step = 10;
+        } else if (f < 4) {
+            const int xx = u & 7, zz = u >> 3;
+            h0 = ((zz + 1) * 10 + (f == 2 ? 0 : 9)) * 10 + (xx + 1);
+            step = 1;
+        } else {
+            const int xx = u & 7, yy = u >> 3;
+            h0 = ((f == 4 ? 0 : 9) * 10 + (yy + 1)) * 10 + (xx + 1);
+            step = 1;
+        }
+        S.psi[h0] = v0;
+        S.psi[h0 + step] = v1;
+    }
+    __syncwarp();
+
+    // ---- the band at the start of the march: finite nodes above the previous
+    // bound, plus ghost nodes the neighbour lowered in restart k-1 (Upsilon)
+    unsigned B = 0, G = 0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int hh = hbase + (j >> 3) * 100 + (j & 7);
+        const T v = S.psi[hh];
+        if (v < INF && static_cast<double>(v) > bprev) {
+            B |= 1u << j;
+            S.psi[hh] = -v;
+        }
+    }
+    auto mark_ghost = [&](int bit, unsigned long long um, int uu) {
+        const int hh = ghost_halo(bit, y, z0);
+        const T g = S.psi[hh];
+        if (g < INF && (((um >> uu) & 1ull) || static_cast<double>(g) > bprev)) {
+            G |= 1u << bit;
+            S.psi[hh] = -g;
+        }
+    };
+    mark_ghost(0, fups[0], z0 * 8 + y);
+    mark_ghost(1, fups[0], (z0 + 1) * 8 + y);
+    mark_ghost(2, fups[1], z0 * 8 + y);
+    mark_ghost(3, fups[1], (z0 + 1) * 8 + y);
+    if (y == 0 || y == 7) {
+        const unsigned long long um = (y == 0) ? fups[2] : fups[3];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) mark_ghost(4 + j, um, (z0 + (j >> 3)) * 8 + (j & 7));
+    }
+    if (zp == 0 || zp == 3) {
+        const unsigned long long um = (zp == 0) ? fups[4] : fups[5];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) mark_ghost(20 + x, um, y * 8 + x);
+    }
+    __syncwarp();
+
+    const T rmin_b = warp_min(rlo);
+    acc.rmin = fminf(acc.rmin, static_cast<float>(rmin_b));
+    acc.rmax = fmaxf(acc.rmax, static_cast<float>(warp_max(rhi)));
+    const double w = P.window * static_cast<double>(rmin_b);
+    const float tau = static_cast<float>(P.fallback_tau);
+
+    // ---- rounds of windowed ordered acceptance
+    unsigned U = 0;                   // own nodes lowered in this march
+    int rounds = 0;
+    for (;;) {
+        T lmin = INF;
+        for (unsigned m = B; m; m &= m - 1) {
+            const int j = __ffs(m) - 1;
+            lmin = vmin(lmin, vabs(S.psi[hbase + (j >> 3) * 100 + (j & 7)]));
+        }
+        for (unsigned m = G; m; m &= m - 1) lmin = vmin(lmin, vabs(S.psi[ghost_halo(__ffs(m) - 1, y, z0)]));
+        const T mn = warp_min(lmin);
+        if (!(static_cast<double>(mn) <= bound)) break;
+        if (++rounds > kRoundCap) {
+            atomicOr(&P.ctrl->status, kStRoundCap);
+            break;
+        }
+        const double thr = fmin(static_cast<double>(mn) + w, bound);
+        unsigned A = 0, AG = 0;
+        for (unsigned m = B; m; m &= m - 1) {
+            const int j = __ffs(m) - 1;
+            const int hh = hbase + (j >> 3) * 100 + (j & 7);
+            const T v = vabs(S.psi[hh]);
+            if (static_cast<double>(v) <= thr) {
+                A |= 1u << j;
+                S.psi[hh] = v;
+            }
+        }
+        for (unsigned m = G; m; m &= m - 1) {
+            const int bit = __ffs(m) - 1;
+            const int hh = ghost_halo(bit, y, z0);
+            const T v = vabs(S.psi[hh]);
+            if (static_cast<double>(v) <= thr) {
+                AG |= 1u << bit;
+                S.psi[hh] = v;
+            }
+        }
+        B &= ~A;
+        G &= ~AG;
+        acc.accepted += __popc(A) + __popc(AG);
+        __syncwarp();
+
+        // Alg. 2: neighbours of the accepted nodes inside the brick
+        unsigned D = ((A << 1) & 0xFEFEu) | ((A >> 1) & 0x7F7Fu);   // x +- 1
+        D |= ((A & 0xFFu) << 8) | (A >> 8);                          // z0 <-> z1 in this lane
+        const unsigned zup = __shfl_down_sync(kFull, A, 8);          // lane with z + 2
+        const unsigned zdn = __shfl_up_sync(kFull, A, 8);            // lane with z - 2
+        if (zp < 3) D |= (zup & 0xFFu) << 8;
+        if (zp > 0) D |= zdn >> 8;
+        const unsigned yup = __shfl_down_sync(kFull, A, 1);          // lane with y + 1
+        const unsigned ydn = __shfl_up_sync(kFull, A, 1);            // lane with y - 1
+        if (y < 7) D |= yup;
+        if (y > 0) D |= ydn;
+        D |= (AG & 1u) | ((AG & 2u) << 7) | ((AG & 4u) << 5) | ((AG & 8u) << 12);
+        D |= (AG >> 4) & 0xFFFFu;
+        if (zp == 0) D |= (AG >> 20) & 0xFFu;
+        if (zp == 3) D |= ((AG >> 20) & 0xFFu) << 8;
+        D &= ~FXOB & 0xFFFFu;
+
+        // compaction of the nodes to re-solve
+        const int cnt = __popc(D);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        int off = incl - cnt;
+        for (unsigned m = D; m; m &= m - 1) {
+            const int j = __ffs(m) - 1;
+            S.list[off++] = static_cast<uint16_t>(pbase + (j >> 3) * 64 + (j & 7));
+        }
+        __syncwarp();
+        acc.solves += total;
+
+        // Alg. 3 for each listed node, 32 at a time; new values land after the reads
+        for (int base = 0; base < total; base += 32) {
+            const int idx = base + lane;
+            bool imp = false;
+            T xn = 0;
+            int hq = 0, q = 0;
+            if (idx < total) {
+                q = S.list[idx];
+                hq = halo_of(q);
+                const T c = vabs(S.psi[hq]);
+                // KNOWN neighbours below the node's current value (Alg. 3's test)
+                auto kn = [&](T v) -> T { return (sgn(v) || !(v < c)) ? INF : v; };
+                T mx = vmin(kn(S.psi[hq - 1]), kn(S.psi[hq + 1]));
+                T my = vmin(kn(S.psi[hq - 10]), kn(S.psi[hq + 10]));
+                T mz = vmin(kn(S.psi[hq - 100]), kn(S.psi[hq + 100]));
+                // reorder psi_1 <= psi_2 <= psi_3
+                T lo = vmin(mx, my), hi = vmax(mx, my);
+                T a0 = vmin(lo, mz);
+                T t1 = vmax(lo, mz);
+                T a1 = vmin(hi, t1), a2 = vmax(hi, t1);
+                if (a0 < INF) {
+                    xn = RootOf<T>::go(a0, a1, a2, S.r[q], tau, acc.fallbacks);
+                    imp = xn < c;
+                }
+            }
+            __syncwarp();
+            if (imp) {
+                S.psi[hq] = -xn;
+                S.newp[q] = 1;
+            }
+            acc.updates += __popc(__ballot_sync(kFull, imp));
+            __syncwarp();
+        }
+
+        // lowered own nodes rejoin the band (Alg. 2: tag BAND)
+        {
+            unsigned long long* np = reinterpret_cast<unsigned long long*>(S.newp);
+            const unsigned long long n0 = np[pbase >> 3], n1 = np[(pbase + 64) >> 3];
+            if (n0 | n1) {
+                const unsigned nb = pack_bytes(n0) | (pack_bytes(n1) << 8);
+                B |= nb;
+                U |= nb;
+                np[pbase >> 3] = 0;
+                np[(pbase + 64) >> 3] = 0;
+            }
+        }
+        __syncwarp();
+    }
+    acc.rounds += rounds;
+
+    // ---- Upsilon: own face nodes lowered in this march, per face (face-local bit masks)
+    unsigned long long um[6];
+    um[0] = (static_cast<unsigned long long>(U & 1u) << (z0 * 8 + y)) |
+            (static_cast<unsigned long long>((U >> 8) & 1u) << ((z0 + 1) * 8 + y));
+    um[1] = (static_cast<unsigned long long>((U >> 7) & 1u) << (z0 * 8 + y)) |
+            (static_cast<unsigned long long>((U >> 15) & 1u) << ((z0 + 1) * 8 + y));
+    um[2] = (y == 0) ? (static_cast<unsigned long long>(U & 0xFFFFu) << (z0 * 8)) : 0ull;
+    um[3] = (y == 7) ? (static_cast<unsigned long long>(U & 0xFFFFu) << (z0 * 8)) : 0ull;
+    um[4] = (zp == 0) ? (static_cast<unsigned long long>(U & 0xFFu) << (y * 8)) : 0ull;
+    um[5] = (zp == 3) ? (static_cast<unsigned long long>((U >> 8) & 0xFFu) << (y * 8)) : 0ull;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) um[f] = warp_or64(um[f]);
+
+    // ---- write the other copy, then publish it
+    const int ns = (st < 0) ? 0 : ((st & 1) ^ 1);
+    T* dst = P.slot + (static_cast<int64_t>(b) * 2 + ns) * kSlot;
+    {
+        T row[8];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+#pragma unroll
+            for (int x = 0; x < 8; ++x) row[x] = vabs(S.psi[hbase + 100 * s + x]);
+            store8(dst + pbase + 64 * s, row);
+            dst[kXF0 + (z0 + s) * 8 + y] = row[0];
+            dst[kXF7 + (z0 + s) * 8 + y] = row[7];
+        }
+    }
+    if (lane < 6) P.ups[(static_cast<int64_t>(b) * 2 + ns) * 6 + lane] = um[lane];
+    if (lane == 0) P.slot_k[2 * b + ns] = k;
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) P.stamp[b] = (k << 1) | ns;
+
+    // ---- activation for restart k+1 (A of Alg. 4/5, C of Alg. 4)
+    const bool pending = __any_sync(kFull, (B | G) != 0u);
+    int32_t* next = ((k + 1) & 1) ? P.list1 : P.list0;
+    auto enqueue = [&](int32_t x) {
+        if (atomicMax(P.queued + x, k + 1) < k + 1) {
+            const int pos = atomicAdd(&P.ctrl->count[(k + 1) & 1], 1);
+            next[pos] = x;
+        }
+    };
+    if (lane == 0 && pending) enqueue(b);
+    if (lane < 6 && um[lane] != 0ull && nbr[lane] >= 0) enqueue(nbr[lane]);
+    acc.band += __popc(B) + __popc(G);
+}
+
+// Grid barrier at the end of restart k.  The CTA arriving last does the
+// restart bookkeeping of Alg. 6 (statistics, exit test, next bound) before
+// releasing the others.  Returns false when this CTA must leave the loop.
+template <typename T>
+__device__ bool end_of_restart(const LoopParams<T>& P) {
+    __shared__ int s_last;
+    __shared__ int s_ok;
+    Ctrl* C = P.ctrl;
+    __syncthreads();
+    unsigned gen = 0;
+    if (threadIdx.x == 0) {
+        gen = ld_acquire(&C->bar_gen);
+        __threadfence();
+        const unsigned arrived = atomicAdd(&C->bar_count, 1u);
+        s_last = (arrived == gridDim.x - 1);
+        s_ok = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_last) {
+            __threadfence();
+            const int k = __ldcg(&C->k);
+            const int par = k & 1;
+            const int n_this = __ldcg(&C->count[par]);
+            const int n_next = __ldcg(&C->count[par ^ 1]);
+            const unsigned long long now = globaltimer();
+            const unsigned long long acc_a = __ldcg(&C->r_accepted), acc_band = __ldcg(&C->r_band);
+            if (P.log != nullptr && k - 1 < P.log_cap) {
+                RestartRec rec;
+                rec.k = k;
+                rec.active = n_this;
+                rec.band = static_cast<int64_t>(acc_band);
+                rec.accepted = static_cast<int64_t>(acc_a);
+                rec.bound = __ldcg(&C->bound);
+                rec.stride = __ldcg(&C->stride);
+                rec.rmin = __uint_as_float(__ldcg(&C->r_rmin_bits));
+                rec.rmax = __uint_as_float(__ldcg(&C->r_rmax_bits));
+                rec.ms = static_cast<double>(now - __ldcg(&C->t_restart)) * 1e-6;
+                P.log[k - 1] = rec;
+            }
+            C->marches += static_cast<unsigned long long>(n_this);
+            C->accepted += acc_a;
+            C->solves += __ldcg(&C->r_solves);
+            C->updates += __ldcg(&C->r_updates);
+            C->fallbacks += __ldcg(&C->r_fallbacks);
+            C->rounds += __ldcg(&C->r_rounds);
+            C->r_accepted = 0;
+            C->r_band = 0;
+            C->r_solves = 0;
+            C->r_updates = 0;
+            C->r_fallbacks = 0;
+            C->r_rounds = 0;
+            C->r_rmin_bits = 0x7f800000u;
+            C->r_rmax_bits = 0u;
+            C->count[par] = 0;
+            C->head[par] = 0;
+            if (n_next == 0) {
+                C->done = 1;
+                C->t_end = now;
+            } else if (k >= P.max_restarts) {
+                C->done = 1;
+                C->status |= kStRestartCap;
+                C->t_end = now;
+            } else {
+                const double s = __ldcg(&C->stride);
+                const double bnd = __ldcg(&C->bound);
+                C->k = k + 1;
+                C->bound_prev = bnd;
+                C->bound = bnd + s;                 // bound_band <- bound_band + stride (width = +inf)
+                C->t_restart = now;
+            }
+            C->bar_count = 0;
+            __threadfence();
+            st_release(&C->bar_gen, gen + 1);
+        } else {
+            long long it = 0;
+            while (ld_acquire(&C->bar_gen) == gen) {
+                if (++it > P.wait_limit) {
+                    atomicOr(&C->status, kStWaitTimeout);
+                    s_ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kWarps * 32) k_restart_loop(LoopParams<T> P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmem<T>& S = reinterpret_cast<WarpSmem<T>*>(smem_raw)[warp];
+    for (int i = lane; i < kBrick / 8; i += 32) reinterpret_cast<unsigned long long*>(S.newp)[i] = 0ull;
+    __syncwarp();
+    Ctrl* C = P.ctrl;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const unsigned long long t0 = globaltimer();
+        C->t_begin = t0;
+        C->t_restart = t0;
+    }
+    for (;;) {
+        const int k = __ldcg(&C->k);
+        const double bound = __ldcg(&C->bound);
+        const double bprev = __ldcg(&C->bound_prev);
+        const int par = k & 1;
+        const int n = __ldcg(&C->count[par]);
+        const int32_t* list = par ? P.list1 : P.list0;
+        MarchAcc acc{0u, 0u, 0, 0ull, 0ull, 0ull, __int_as_float(0x7f800000), 0.0f};
+        bool any = false;
+        for (;;) {
+            int i = 0;
+            if (lane == 0) i = atomicAdd(&C->head[par], 1);
+            i = __shfl_sync(kFull, i, 0);
+            if (i >= n) break;
+            march_brick<T>(P, S, __ldcg(list + i), k, bprev, bound, lane, acc);
+            any = true;
+        }
+        if (any) {
+            const unsigned acc_a = __reduce_add_sync(kFull, acc.accepted);
+            const unsigned acc_b = __reduce_add_sync(kFull, acc.band);
+            const int fb = __reduce_add_sync(kFull, acc.fallbacks);
+            if (lane == 0) {
+                atomicAdd(&C->r_accepted, static_cast<unsigned long long>(acc_a));
+                atomicAdd(&C->r_band, static_cast<unsigned long long>(acc_b));
+                atomicAdd(&C->r_solves, acc.solves);
+                atomicAdd(&C->r_updates, acc.updates);
+                atomicAdd(&C->r_rounds, acc.rounds);
+                atomicMin(&C->r_rmin_bits, __float_as_uint(acc.rmin));
+                atomicMax(&C->r_rmax_bits, __float_as_uint(acc.rmax));
+                if (fb) atomicAdd(&C->r_fallbacks, static_cast<unsigned long long>(fb));
+            }
+        }
+        if (!end_of_restart<T>(P)) return;
+        if (__ldcg(&C->done)) return;
+    }
+}
+
+// F (x fastest) -> h/F in brick layout; flags negative, NaN or infinite speeds.
+template <typename T>
+__global__ void k_layout_speed(const T* __restrict__ F, T* __restrict__ rr, int nx, int ny, int nz, int BX,
+                               int BY, int64_t nbricks, double h, int* err) {
+    const int64_t total = nbricks * kBrick;
+    const T INF = Num<T>::inf();
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t b = t >> 9;
+        const int p = static_cast<int>(t & 511);
+        const int bx = static_cast<int>(b % BX), by = static_cast<int>((b / BX) % BY),
+                  bz = static_cast<int>(b / (static_cast<int64_t>(BX) * BY));
+        const int i = bx * 8 + (p & 7), j = by * 8 + ((p >> 3) & 7), k = bz * 8 + (p >> 6);
+        T r = INF;
+        if (i < nx && j < ny && k < nz) {
+            const T f = F[(static_cast<int64_t>(k) * ny + j) * nx + i];
+            if (!(f >= 0) || !(f < INF)) atomicOr(err, 1);
+            else if (f > 0) r = static_cast<T>(h / static_cast<double>(f));
+        }
+        rr[t] = r;
+    }
+}
+
+// Alg. 1 for the bricks that hold fixed nodes, and the work list of restart 1.
+//   fix_b/fix_p/fix_v: fixed nodes (brick, node in brick, psi0); saved_r gets their h/F.
+template <typename T>
+__global__ void k_init_sources(int nfix, const int32_t* __restrict__ fix_b, const int32_t* __restrict__ fix_p,
+                               const double* __restrict__ fix_v, int nsrcb, const int32_t* __restrict__ src_bricks,
+                               int nenq, const int32_t* __restrict__ enq, T* slot, int32_t* slot_k,
+                               unsigned long long* ups, int32_t* stamp, int32_t* queued, T* rr, T* saved_r,
+                               int32_t* list1) {
+    const T INF = Num<T>::inf();
+    if (blockIdx.x < nsrcb) {
+        const int32_t b = src_bricks[blockIdx.x];
+        T* dst = slot + static_cast<int64_t>(b) * 2 * kSlot;            // copy 0
+        for (int t = threadIdx.x; t < kSlot; t += blockDim.x) dst[t] = INF;
+        __syncthreads();
+        for (int t = threadIdx.x; t < nfix; t += blockDim.x) {
+            if (fix_b[t] != b) continue;
+            const int p = fix_p[t];
+            const T v = static_cast<T>(fix_v[t]);
+            dst[p] = v;
+            const int x = p & 7, y = (p >> 3) & 7, z = p >> 6;
+            if (x == 0) dst[kXF0 + z * 8 + y] = v;
+            if (x == 7) dst[kXF7 + z * 8 + y] = v;
+        }
+        if (threadIdx.x < 6) ups[static_cast<int64_t>(b) * 2 * 6 + threadIdx.x] = 0ull;
+        if (threadIdx.x == 0) {
+            slot_k[2 * b] = 0;
+            stamp[b] = 0;
+        }
+    } else {
+        const int base = (blockIdx.x - nsrcb) * blockDim.x + threadIdx.x;
+        if (base < nfix) {
+            const int64_t g = static_cast<int64_t>(fix_b[base]) * kBrick + fix_p[base];
+            saved_r[base] = rr[g];
+            rr[g] = static_cast<T>(-1);
+        }
+        if (base < nenq) {
+            list1[base] = enq[base];
+            queued[enq[base]] = 1;
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_restore_r(int nfix, const int32_t* __restrict__ fix_b, const int32_t* __restrict__ fix_p,
+                            const T* __restrict__ saved_r, T* rr) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nfix) rr[static_cast<int64_t>(fix_b[t]) * kBrick + fix_p[t]] = saved_r[t];
+}
+
+// h/F of selected nodes (brick, node) for the host's source set-up.
+template <typename T>
+__global__ void k_gather_r(int n, const int32_t* __restrict__ nb_b, const int32_t* __restrict__ nb_p,
+                           const T* __restrict__ rr, double* out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = static_cast<double>(rr[static_cast<int64_t>(nb_b[t]) * kBrick + nb_p[t]]);
+}
+
+// Latest copy of every brick -> psi in x-fastest order, nodes z in [z_begin, z_end).
+template <typename T>
+__global__ void k_result(const T* __restrict__ slot, const int32_t* __restrict__ stamp, T* __restrict__ out, int nx,
+                         int ny, int z_begin, int z_end, int BX, int BY) {
+    const T INF = Num<T>::inf();
+    const int64_t plane = static_cast<int64_t>(nx) * ny;
+    const int64_t total = plane * (z_end - z_begin);
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int k = z_begin + static_cast<int>(t / plane);
+        const int64_t rem = t % plane;
+        const int j = static_cast<int>(rem / nx), i = static_cast<int>(rem % nx);
+        const int64_t b = (static_cast<int64_t>(k >> 3) * BY + (j >> 3)) * BX + (i >> 3);
+        const int p = ((k & 7) * 8 + (j & 7)) * 8 + (i & 7);
+        const int32_t st = stamp[b];
+        out[t] = (st < 0) ? INF : slot[(b * 2 + (st & 1)) * kSlot + p];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launch helpers (called from eik_runtime.cu)
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_layout_speed(const T* F, T* rr, int nx, int ny, int nz, int BX, int BY, int64_t nbricks,
+                                double h, int* err, cudaStream_t s) {
+    const int64_t total = nbricks * kBrick;
+    int grid = static_cast<int>((total + 255) / 256);
+    if (grid > 65535 * 4) grid = 65535 * 4;
+    k_layout_speed<T><<<grid, 256, 0, s>>>(F, rr, nx, ny, nz, BX, BY, nbricks, h, err);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_init_sources(int nfix, const int32_t* fix_b, const int32_t* fix_p, const double* fix_v,
+                                int nsrcb, const int32_t* src_bricks, int nenq, const int32_t* enq, T* slot,
+                                int32_t* slot_k, unsigned long long* ups, int32_t* stamp, int32_t* queued, T* rr,
+                                T* saved_r, int32_t* list1, cudaStream_t s) {
+    const int m = nfix > nenq ? nfix : nenq;
+    const int grid = nsrcb + (m + 255) / 256;
+    k_init_sources<T><<<grid, 256, 0, s>>>(nfix, fix_b, fix_p, fix_v, nsrcb, src_bricks, nenq, enq, slot, slot_k,
+                                           ups, stamp, queued, rr, saved_r, list1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_restore_r(int nfix, const int32_t* fix_b, const int32_t* fix_p, const T* saved_r, T* rr,
+                             cudaStream_t s) {
+    if (nfix <= 0) return cudaSuccess;
+    k_restore_r<T><<<(nfix + 255) / 256, 256, 0, s>>>(nfix, fix_b, fix_p, saved_r, rr);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gather_r(int n, const int32_t* nb_b, const int32_t* nb_p, const T* rr, double* out,
+                            cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_gather_r<T><<<(n + 255) / 256, 256, 0, s>>>(n, nb_b, nb_p, rr, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_result(const T* slot, const int32_t* stamp, T* out, int nx, int ny, int z_begin, int z_end,
+                          int BX, int BY, cudaStream_t s) {
+    const int64_t total = static_cast<int64_t>(nx) * ny * (z_end - z_begin);
+    int grid = static_cast<int>((total + 255) / 256);
+    if (grid > 65535 * 4) grid = 65535 * 4;
+    if (grid < 1) grid = 1;
+    k_result<T><<<grid, 256, 0, s>>>(slot, stamp, out, nx, ny, z_begin, z_end, BX, BY);
+    return cudaGetLastError();
+}
+
+template <typename T>
+size_t loop_smem_bytes() {
+    return sizeof(WarpSmem<T>) * kWarps;
+}
+
+template <typename T>
+cudaError_t loop_occupancy(int* blocks_per_sm) {
+    const size_t smem = loop_smem_bytes<T>();
+    cudaError_t e = cudaFuncSetAttribute(k_restart_loop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_restart_loop<T>, kWarps * 32, smem);
+}
+
+template <typename T>
+cudaError_t launch_restart_loop(const LoopParams<T>& P, int grid, cudaStream_t s) {
+    LoopParams<T> copy = P;
+    void* args[] = {&copy};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_restart_loop<T>), dim3(grid),
+                                       dim3(kWarps * 32), args, loop_smem_bytes<T>(), s);
+}
+
+#define EIKG_INSTANTIATE(T)                                                                                     \
+    template cudaError_t launch_layout_speed<T>(const T*, T*, int, int, int, int, int, int64_t, double, int*,    \
+                                                cudaStream_t);                                                   \
+    template cudaError_t launch_init_sources<T>(int, const int32_t*, const int32_t*, const double*, int,         \
+                                                const int32_t*, int, const int32_t*, T*, int32_t*,                \
+                                                unsigned long long*, int32_t*, int32_t*, T*, T*, int32_t*,        \
+                                                cudaStream_t);                                                   \
+    template cudaError_t launch_restore_r<T>(int, const int32_t*, const int32_t*, const T*, T*, cudaStream_t);   \
+    template cudaError_t launch_gather_r<T>(int, const int32_t*, const int32_t*, const T*, double*,              \
+                                            cudaStream_t);                                                       \
+    template cudaError_t launch_result<T>(const T*, const int32_t*, T*, int, int, int, int, int, int,            \
+                                          cudaStream_t);                                                         \
+    template size_t loop_smem_bytes<T>();                                                                        \
+    template cudaError_t loop_occupancy<T>(int*);                                                                \
+    template cudaError_t launch_restart_loop<T>(const LoopParams<T>&, int, cudaStream_t);
+
+EIKG_INSTANTIATE(float)
+EIKG_INSTANTIATE(double)
+
+}  // namespace eikg

@@ -1,0 +1,622 @@
+// Host runtime of libeik: the C ABI declared in include/eik.h.
+//
+// A context owns the device copy of h/F in brick layout, the two psi copies of
+// every brick, the work lists and the control block of the restart loop.  A
+// solve (Alg. 6) is: reset the per-brick state, set up the fixed nodes of the
+// point sources (Alg. 1), run the cooperative restart-loop kernel, restore h/F
+// at the fixed nodes.  Everything runs on the context's stream.
+#include "eik.h"
+#include "eik_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace eikg {
+template <typename T>
+cudaError_t launch_layout_speed(const T*, T*, int, int, int, int, int, int64_t, double, int*, cudaStream_t);
+template <typename T>
+cudaError_t launch_init_sources(int, const int32_t*, const int32_t*, const double*, int, const int32_t*, int,
+                                const int32_t*, T*, int32_t*, unsigned long long*, int32_t*, int32_t*, T*, T*,
+                                int32_t*, cudaStream_t);
+template <typename T>
+cudaError_t launch_restore_r(int, const int32_t*, const int32_t*, const T*, T*, cudaStream_t);
+template <typename T>
+cudaError_t launch_gather_r(int, const int32_t*, const int32_t*, const T*, double*, cudaStream_t);
+template <typename T>
+cudaError_t launch_result(const T*, const int32_t*, T*, int, int, int, int, int, int, cudaStream_t);
+template <typename T>
+size_t loop_smem_bytes();
+template <typename T>
+cudaError_t loop_occupancy(int*);
+template <typename T>
+cudaError_t launch_restart_loop(const LoopParams<T>&, int, cudaStream_t);
+}  // namespace eikg
+
+using eikg::kBrick;
+using eikg::kSlot;
+
+struct eik_ctx {
+    int nx = 0, ny = 0, nz = 0;
+    double h = 0;
+    eik_precision prec = EIK_FP32;
+    cudaStream_t stream = nullptr;
+    int BX = 0, BY = 0, BZ = 0;
+    int64_t nbricks = 0;
+    size_t esz = 4;
+    void* rr = nullptr;
+    void* slot = nullptr;
+    int32_t* slot_k = nullptr;
+    unsigned long long* ups = nullptr;
+    int32_t* stamp = nullptr;
+    int32_t* queued = nullptr;
+    int32_t* list0 = nullptr;
+    int32_t* list1 = nullptr;
+    eikg::Ctrl* ctrl = nullptr;
+    int* err_flag = nullptr;
+    eikg::RestartRec* log = nullptr;
+    int64_t log_cap = 0;
+    void* scratch = nullptr;       // per-solve tables of the fixed nodes
+    size_t scratch_cap = 0;
+    void* fstage = nullptr;        // staging for host speed uploads and host results
+    size_t fstage_cap = 0;
+    int nfix = 0;
+    int32_t* d_fix_b = nullptr;
+    int32_t* d_fix_p = nullptr;
+    void* d_saved_r = nullptr;
+    std::vector<double> src;
+    bool solved = false;
+    bool in_flight = false;
+    int64_t last_nr = 0;
+    int loop_grid = 0;
+    int sms = 0;
+    eik_params params{};
+    eikg::Ctrl host_ctrl{};
+    std::string err;
+};
+
+namespace {
+
+std::string g_create_error;
+
+eik_status fail(eik_ctx* c, eik_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+#define EIK_CK(ctx, call)                                                                                   \
+    do {                                                                                                    \
+        cudaError_t e_ = (call);                                                                            \
+        if (e_ != cudaSuccess)                                                                              \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? EIK_ENOMEM : EIK_ECUDA,                    \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                                \
+    } while (0)
+
+template <typename P>
+cudaError_t dalloc(P** p, size_t bytes) {
+    return cudaMalloc(reinterpret_cast<void**>(p), bytes < 16 ? 16 : bytes);
+}
+
+void free_all(eik_ctx* c) {
+    void* ptrs[] = {c->rr,    c->slot,  c->slot_k, c->ups,   c->stamp,   c->queued, c->list0, c->list1,
+                    c->ctrl,  c->err_flag, c->log, c->scratch, c->fstage};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+// F (x fastest, caller memory) -> h/F in brick layout, with validation.
+eik_status upload_speed(eik_ctx* c, const void* F, int F_on_device) {
+    const size_t bytes = static_cast<size_t>(c->nx) * c->ny * c->nz * c->esz;
+    const void* Fd = F;
+    if (!F_on_device) {
+        if (bytes > c->fstage_cap) {
+            if (c->fstage) cudaFree(c->fstage);
+            c->fstage = nullptr;
+            c->fstage_cap = 0;
+            EIK_CK(c, cudaMalloc(&c->fstage, bytes));
+            c->fstage_cap = bytes;
+        }
+        EIK_CK(c, cudaMemcpyAsync(c->fstage, F, bytes, cudaMemcpyHostToDevice, c->stream));
+        Fd = c->fstage;
+    }
+    EIK_CK(c, cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->stream));
+    if (c->prec == EIK_FP32)
+        EIK_CK(c, eikg::launch_layout_speed<float>(static_cast<const float*>(Fd), static_cast<float*>(c->rr), c->nx,
+                                                   c->ny, c->nz, c->BX, c->BY, c->nbricks, c->h, c->err_flag,
+                                                   c->stream));
+    else
+        EIK_CK(c, eikg::launch_layout_speed<double>(static_cast<const double*>(Fd), static_cast<double*>(c->rr),
+                                                    c->nx, c->ny, c->nz, c->BX, c->BY, c->nbricks, c->h,
+                                                    c->err_flag, c->stream));
+    int bad = 0;
+    EIK_CK(c, cudaMemcpyAsync(&bad, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    EIK_CK(c, cudaStreamSynchronize(c->stream));
+    if (bad) return fail(c, EIK_EINVAL, "F must be finite and >= 0 everywhere");
+    return EIK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* eik_version(void) { return "eik-gb300 0.1 (sm_103a)"; }
+
+const char* eik_last_error(const eik_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+void eik_params_default(eik_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->stride = 0.0;
+    p->block_dim = 8;
+    p->schedule = EIK_SCHED_FIXED;
+    p->window = 1.0 / std::sqrt(3.0);
+    p->fallback_tau = 0.125;
+    p->max_restarts = int64_t(1) << 24;
+    p->log_restarts = 0;
+}
+
+eik_status eik_create(eik_ctx** out, const int32_t dims[3], double h, const void* F, int F_on_device,
+                      eik_precision precision, void* stream) {
+    if (!out) return fail(nullptr, EIK_EINVAL, "eik_create: out is NULL");
+    *out = nullptr;
+    if (!dims) return fail(nullptr, EIK_EINVAL, "eik_create: dims is NULL");
+    if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1)
+        return fail(nullptr, EIK_EINVAL, "eik_create: every dimension must be >= 1");
+    const int64_t N = int64_t(dims[0]) * dims[1] * dims[2];
+    if (N >= (int64_t(1) << 31)) return fail(nullptr, EIK_EINVAL, "eik_create: nx*ny*nz must be < 2^31");
+    if (!finite_pos(h)) return fail(nullptr, EIK_EINVAL, "eik_create: h must be finite and > 0");
+    if (!F) return fail(nullptr, EIK_EINVAL, "eik_create: F is NULL");
+    if (precision != EIK_FP32 && precision != EIK_FP64)
+        return fail(nullptr, EIK_EINVAL, "eik_create: precision must be EIK_FP32 or EIK_FP64");
+
+    eik_ctx* c = new (std::nothrow) eik_ctx();
+    if (!c) return fail(nullptr, EIK_ENOMEM, "eik_create: host allocation failed");
+    c->nx = dims[0];
+    c->ny = dims[1];
+    c->nz = dims[2];
+    c->h = h;
+    c->prec = precision;
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->esz = precision == EIK_FP32 ? 4 : 8;
+    c->BX = (c->nx + 7) / 8;
+    c->BY = (c->ny + 7) / 8;
+    c->BZ = (c->nz + 7) / 8;
+    c->nbricks = int64_t(c->BX) * c->BY * c->BZ;
+    eik_params_default(&c->params);
+
+    auto bail = [&](eik_status s, const std::string& m) {
+        free_all(c);
+        delete c;
+        return fail(nullptr, s, m);
+    };
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return bail(EIK_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!coop) return bail(EIK_ENOTSUP, "eik_create: device lacks cooperative launch");
+    const size_t nb = static_cast<size_t>(c->nbricks);
+    struct {
+        void** p;
+        size_t bytes;
+    } allocs[] = {
+        {&c->rr, nb * kBrick * c->esz},
+        {&c->slot, nb * 2 * kSlot * c->esz},
+        {reinterpret_cast<void**>(&c->slot_k), nb * 2 * sizeof(int32_t)},
+        {reinterpret_cast<void**>(&c->ups), nb * 2 * 6 * sizeof(unsigned long long)},
+        {reinterpret_cast<void**>(&c->stamp), nb * sizeof(int32_t)},
+        {reinterpret_cast<void**>(&c->queued), nb * sizeof(int32_t)},
+        {reinterpret_cast<void**>(&c->list0), nb * sizeof(int32_t)},
+        {reinterpret_cast<void**>(&c->list1), nb * sizeof(int32_t)},
+        {reinterpret_cast<void**>(&c->ctrl), sizeof(eikg::Ctrl)},
+        {reinterpret_cast<void**>(&c->err_flag), sizeof(int)},
+    };
+    for (auto& a : allocs) {
+        e = dalloc(a.p, a.bytes);
+        if (e != cudaSuccess)
+            return bail(EIK_ENOMEM, std::string("eik_create: cudaMalloc of ") + std::to_string(a.bytes) +
+                                        " bytes failed: " + cudaGetErrorString(e));
+    }
+    {
+        const eik_status st = upload_speed(c, F, F_on_device);
+        if (st != EIK_OK) {
+            const std::string m = c->err;
+            return bail(st, m);
+        }
+    }
+    int per_sm = 0;
+    e = (c->prec == EIK_FP32) ? eikg::loop_occupancy<float>(&per_sm) : eikg::loop_occupancy<double>(&per_sm);
+    if (e != cudaSuccess || per_sm < 1)
+        return bail(EIK_ECUDA, std::string("eik_create: occupancy query: ") + cudaGetErrorString(e));
+    c->loop_grid = per_sm * c->sms;
+    *out = c;
+    return EIK_OK;
+}
+
+eik_status eik_set_speed(eik_ctx* c, const void* F, int F_on_device) {
+    if (!c) return fail(nullptr, EIK_EINVAL, "eik_set_speed: ctx is NULL");
+    if (!F) return fail(c, EIK_EINVAL, "eik_set_speed: F is NULL");
+    if (c->in_flight) return fail(c, EIK_ESTATE, "eik_set_speed: a solve is in flight (call eik_wait)");
+    c->solved = false;
+    return upload_speed(c, F, F_on_device);
+}
+
+eik_status eik_add_sources(eik_ctx* c, int32_t n, const double* xyz) {
+    if (!c) return fail(nullptr, EIK_EINVAL, "eik_add_sources: ctx is NULL");
+    if (c->in_flight) return fail(c, EIK_ESTATE, "eik_add_sources: a solve is in flight (call eik_wait)");
+    if (n < 0) return fail(c, EIK_EINVAL, "eik_add_sources: n < 0");
+    if (n > 0 && !xyz) return fail(c, EIK_EINVAL, "eik_add_sources: xyz is NULL");
+    const int dims[3] = {c->nx, c->ny, c->nz};
+    const double tol = 1e-9 * c->h;
+    for (int s = 0; s < n; ++s)
+        for (int a = 0; a < 3; ++a) {
+            const double v = xyz[3 * s + a];
+            const double ext = (dims[a] - 1) * c->h;
+            if (!std::isfinite(v) || v < -tol || v > ext + tol)
+                return fail(c, EIK_EINVAL, "eik_add_sources: source " + std::to_string(s) + " lies outside the grid");
+        }
+    c->src.insert(c->src.end(), xyz, xyz + 3 * static_cast<size_t>(n));
+    return EIK_OK;
+}
+
+eik_status eik_clear_sources(eik_ctx* c) {
+    if (!c) return fail(nullptr, EIK_EINVAL, "eik_clear_sources: ctx is NULL");
+    if (c->in_flight) return fail(c, EIK_ESTATE, "eik_clear_sources: a solve is in flight");
+    c->src.clear();
+    return EIK_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Nodes of the cell containing coordinate s along one axis (Alg. 1, "on or
+// adjacent to Gamma"): one node when s is within 1e-9 cells of a node.
+int cell_nodes(double s, double h, int n, int out[2]) {
+    const double t = s / h;
+    const double tn = std::floor(t + 0.5);
+    if (std::fabs(t - tn) <= 1e-9) {
+        out[0] = std::min(std::max(static_cast<int>(tn), 0), n - 1);
+        return 1;
+    }
+    const int i0 = std::min(std::max(static_cast<int>(std::floor(t)), 0), std::max(n - 2, 0));
+    out[0] = i0;
+    out[1] = std::min(i0 + 1, n - 1);
+    return (out[1] == out[0]) ? 1 : 2;
+}
+
+struct FixNode {
+    int32_t b, p;
+    double v;
+};
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+template <typename T>
+eik_status queue_solve(eik_ctx* c, const eik_params& P) {
+    cudaStream_t s = c->stream;
+    // ---- fixed nodes: candidates of every source, with their h/F from the device
+    struct Cand {
+        int i, j, k;
+        double dist;
+    };
+    std::vector<Cand> cand;
+    const int nsrc = static_cast<int>(c->src.size() / 3);
+    for (int q = 0; q < nsrc; ++q) {
+        const double* xs = &c->src[3 * q];
+        int ci[3][2], cn[3];
+        cn[0] = cell_nodes(xs[0], c->h, c->nx, ci[0]);
+        cn[1] = cell_nodes(xs[1], c->h, c->ny, ci[1]);
+        cn[2] = cell_nodes(xs[2], c->h, c->nz, ci[2]);
+        for (int a = 0; a < cn[2]; ++a)
+            for (int bq = 0; bq < cn[1]; ++bq)
+                for (int d = 0; d < cn[0]; ++d) {
+                    const int i = ci[0][d], j = ci[1][bq], k = ci[2][a];
+                    const double dx = i * c->h - xs[0], dy = j * c->h - xs[1], dz = k * c->h - xs[2];
+                    cand.push_back({i, j, k, std::sqrt(dx * dx + dy * dy + dz * dz)});
+                }
+    }
+    const int nc = static_cast<int>(cand.size());
+    std::vector<int32_t> cb(nc), cp(nc);
+    for (int t = 0; t < nc; ++t) {
+        cb[t] = ((cand[t].k >> 3) * c->BY + (cand[t].j >> 3)) * c->BX + (cand[t].i >> 3);
+        cp[t] = ((cand[t].k & 7) * 8 + (cand[t].j & 7)) * 8 + (cand[t].i & 7);
+    }
+    // scratch: candidate tables, then the fixed-node tables
+    const size_t need = align_up(nc * 4) * 2 + align_up(nc * 8) + align_up(nc * 4) * 4 + align_up(nc * 8) +
+                        align_up(nc * sizeof(T)) + 4096;
+    if (need > c->scratch_cap) {
+        if (c->scratch) cudaFree(c->scratch);
+        c->scratch = nullptr;
+        c->scratch_cap = 0;
+        EIK_CK(c, cudaMalloc(&c->scratch, need));
+        c->scratch_cap = need;
+    }
+    char* sp = static_cast<char*>(c->scratch);
+    auto carve = [&](size_t bytes) {
+        char* r = sp;
+        sp += align_up(bytes);
+        return r;
+    };
+    int32_t* d_cb = reinterpret_cast<int32_t*>(carve(nc * 4));
+    int32_t* d_cp = reinterpret_cast<int32_t*>(carve(nc * 4));
+    double* d_cr = reinterpret_cast<double*>(carve(nc * 8));
+    std::vector<double> cr(nc);
+    if (nc > 0) {
+        EIK_CK(c, cudaMemcpyAsync(d_cb, cb.data(), nc * 4, cudaMemcpyHostToDevice, s));
+        EIK_CK(c, cudaMemcpyAsync(d_cp, cp.data(), nc * 4, cudaMemcpyHostToDevice, s));
+        EIK_CK(c, eikg::launch_gather_r<T>(nc, d_cb, d_cp, static_cast<const T*>(c->rr), d_cr, s));
+        EIK_CK(c, cudaMemcpyAsync(cr.data(), d_cr, nc * 8, cudaMemcpyDeviceToHost, s));
+        EIK_CK(c, cudaStreamSynchronize(s));
+    }
+    std::vector<FixNode> fix;
+    for (int t = 0; t < nc; ++t) {
+        double v;
+        if (cand[t].dist == 0.0) v = 0.0;
+        else if (std::isfinite(cr[t]) && cr[t] > 0.0) v = cand[t].dist * cr[t] / c->h;   // distance / F
+        else continue;                                                                   // barrier node
+        fix.push_back({cb[t], cp[t], v});
+    }
+    std::sort(fix.begin(), fix.end(), [](const FixNode& a, const FixNode& b) {
+        return a.b != b.b ? a.b < b.b : (a.p != b.p ? a.p < b.p : a.v < b.v);
+    });
+    std::vector<FixNode> uf;
+    for (const auto& f : fix)
+        if (uf.empty() || uf.back().b != f.b || uf.back().p != f.p) uf.push_back(f);
+    // bricks holding fixed nodes, and the work list of restart 1: those bricks and
+    // the neighbours whose ghost layer holds a fixed node (Alg. 1 runs over Xi^ib)
+    std::vector<int32_t> sb, enq;
+    for (const auto& f : uf) {
+        if (sb.empty() || sb.back() != f.b) sb.push_back(f.b);
+        enq.push_back(f.b);
+        const int x = f.p & 7, y = (f.p >> 3) & 7, z = f.p >> 6;
+        const int bx = f.b % c->BX, by = (f.b / c->BX) % c->BY, bz = f.b / (c->BX * c->BY);
+        if (x == 0 && bx > 0) enq.push_back(f.b - 1);
+        if (x == 7 && bx < c->BX - 1) enq.push_back(f.b + 1);
+        if (y == 0 && by > 0) enq.push_back(f.b - c->BX);
+        if (y == 7 && by < c->BY - 1) enq.push_back(f.b + c->BX);
+        if (z == 0 && bz > 0) enq.push_back(f.b - c->BX * c->BY);
+        if (z == 7 && bz < c->BZ - 1) enq.push_back(f.b + c->BX * c->BY);
+    }
+    std::sort(enq.begin(), enq.end());
+    enq.erase(std::unique(enq.begin(), enq.end()), enq.end());
+    const int nfix = static_cast<int>(uf.size());
+    std::vector<int32_t> fb(nfix), fp(nfix);
+    std::vector<double> fv(nfix);
+    for (int t = 0; t < nfix; ++t) {
+        fb[t] = uf[t].b;
+        fp[t] = uf[t].p;
+        fv[t] = uf[t].v;
+    }
+    c->d_fix_b = reinterpret_cast<int32_t*>(carve(nfix * 4));
+    c->d_fix_p = reinterpret_cast<int32_t*>(carve(nfix * 4));
+    double* d_fv = reinterpret_cast<double*>(carve(nfix * 8));
+    int32_t* d_sb = reinterpret_cast<int32_t*>(carve(sb.size() * 4));
+    int32_t* d_enq = reinterpret_cast<int32_t*>(carve(enq.size() * 4));
+    c->d_saved_r = carve(nfix * sizeof(T));
+    c->nfix = nfix;
+    if (nfix > 0) {
+        EIK_CK(c, cudaMemcpyAsync(c->d_fix_b, fb.data(), nfix * 4, cudaMemcpyHostToDevice, s));
+        EIK_CK(c, cudaMemcpyAsync(c->d_fix_p, fp.data(), nfix * 4, cudaMemcpyHostToDevice, s));
+        EIK_CK(c, cudaMemcpyAsync(d_fv, fv.data(), nfix * 8, cudaMemcpyHostToDevice, s));
+        EIK_CK(c, cudaMemcpyAsync(d_sb, sb.data(), sb.size() * 4, cudaMemcpyHostToDevice, s));
+        EIK_CK(c, cudaMemcpyAsync(d_enq, enq.data(), enq.size() * 4, cudaMemcpyHostToDevice, s));
+    }
+    // ---- Alg. 1 for every brick: untouched (psi = +inf) unless it holds fixed nodes
+    const size_t nb = static_cast<size_t>(c->nbricks);
+    EIK_CK(c, cudaMemsetAsync(c->stamp, 0xFF, nb * sizeof(int32_t), s));
+    EIK_CK(c, cudaMemsetAsync(c->queued, 0xFF, nb * sizeof(int32_t), s));
+    EIK_CK(c, cudaMemsetAsync(c->slot_k, 0xFF, nb * 2 * sizeof(int32_t), s));
+    if (nfix > 0)
+        EIK_CK(c, eikg::launch_init_sources<T>(nfix, c->d_fix_b, c->d_fix_p, d_fv, static_cast<int>(sb.size()), d_sb,
+                                               static_cast<int>(enq.size()), d_enq, static_cast<T*>(c->slot),
+                                               c->slot_k, c->ups, c->stamp, c->queued, static_cast<T*>(c->rr),
+                                               static_cast<T*>(c->d_saved_r), c->list1, s));
+    // ---- control block: restart 1 with bound_1 = 0 + stride
+    eikg::Ctrl& H = c->host_ctrl;
+    std::memset(&H, 0, sizeof(H));
+    H.k = enq.empty() ? 0 : 1;
+    H.bound_prev = -1.0;
+    H.stride = P.stride;
+    H.bound = 0.0 + P.stride;
+    H.count[1] = static_cast<int32_t>(enq.size());
+    H.r_rmin_bits = 0x7f800000u;
+    H.done = enq.empty() ? 1 : 0;
+    EIK_CK(c, cudaMemcpyAsync(c->ctrl, &H, sizeof(H), cudaMemcpyHostToDevice, s));
+    if (P.log_restarts) {
+        const int64_t want = std::min<int64_t>(P.max_restarts, int64_t(1) << 16);
+        if (want > c->log_cap) {
+            if (c->log) cudaFree(c->log);
+            c->log = nullptr;
+            c->log_cap = 0;
+            EIK_CK(c, cudaMalloc(&c->log, sizeof(eikg::RestartRec) * want));
+            c->log_cap = want;
+        }
+    }
+    if (!enq.empty()) {
+        eikg::LoopParams<T> L{};
+        L.nx = c->nx;
+        L.ny = c->ny;
+        L.nz = c->nz;
+        L.BX = c->BX;
+        L.BY = c->BY;
+        L.BZ = c->BZ;
+        L.nbricks = c->nbricks;
+        L.slot = static_cast<T*>(c->slot);
+        L.slot_k = c->slot_k;
+        L.ups = c->ups;
+        L.stamp = c->stamp;
+        L.queued = c->queued;
+        L.rr = static_cast<const T*>(c->rr);
+        L.list0 = c->list0;
+        L.list1 = c->list1;
+        L.ctrl = c->ctrl;
+        L.log = P.log_restarts ? c->log : nullptr;
+        L.log_cap = P.log_restarts ? c->log_cap : 0;
+        L.window = P.window;
+        L.fallback_tau = P.fallback_tau;
+        L.max_restarts = P.max_restarts;
+        L.wait_limit = (long long)1 << 26;
+        L.sched = P.schedule;
+        L.mlp = nullptr;
+        L.h = c->h;
+        if (P.loop_events[0]) EIK_CK(c, cudaEventRecord(static_cast<cudaEvent_t>(P.loop_events[0]), s));
+        EIK_CK(c, eikg::launch_restart_loop<T>(L, c->loop_grid, s));
+        if (P.loop_events[1]) EIK_CK(c, cudaEventRecord(static_cast<cudaEvent_t>(P.loop_events[1]), s));
+    }
+    if (nfix > 0)
+        EIK_CK(c, eikg::launch_restore_r<T>(nfix, c->d_fix_b, c->d_fix_p, static_cast<const T*>(c->d_saved_r),
+                                            static_cast<T*>(c->rr), s));
+    return EIK_OK;
+}
+
+eik_status check_params(eik_ctx* c, const eik_params* p) {
+    if (!p) return fail(c, EIK_EINVAL, "params is NULL");
+    if (!(p->stride > 0.0)) return fail(c, EIK_EINVAL, "stride must be > 0 (+inf allowed)");
+    if (p->block_dim != 0 && p->block_dim != 8) return fail(c, EIK_ENOTSUP, "block_dim must be 8 (or 0)");
+    if (p->schedule != EIK_SCHED_FIXED) return fail(c, EIK_ENOTSUP, "only the fixed-stride schedule is available");
+    if (!(p->window >= 0.0) || !std::isfinite(p->window)) return fail(c, EIK_EINVAL, "window must be finite and >= 0");
+    if (!(p->fallback_tau >= 0.0) || !(p->fallback_tau <= 1.0))
+        return fail(c, EIK_EINVAL, "fallback_tau must lie in [0, 1]");
+    if (p->max_restarts < 0) return fail(c, EIK_EINVAL, "max_restarts must be >= 0");
+    return EIK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+eik_status eik_solve_async(eik_ctx* c, const eik_params* params) {
+    if (!c) return fail(nullptr, EIK_EINVAL, "eik_solve_async: ctx is NULL");
+    if (c->in_flight) return fail(c, EIK_ESTATE, "eik_solve_async: a solve is already in flight");
+    eik_status st = check_params(c, params);
+    if (st != EIK_OK) return st;
+    if (c->src.empty()) return fail(c, EIK_ESTATE, "eik_solve: no source added");
+    eik_params P = *params;
+    if (P.block_dim == 0) P.block_dim = 8;
+    if (P.max_restarts == 0) P.max_restarts = int64_t(1) << 24;
+    if (P.window == 0.0) P.window = 1.0 / std::sqrt(3.0);
+    c->params = P;
+    st = (c->prec == EIK_FP32) ? queue_solve<float>(c, P) : queue_solve<double>(c, P);
+    if (st != EIK_OK) return st;
+    c->in_flight = true;
+    c->solved = false;
+    return EIK_OK;
+}
+
+eik_status eik_wait(eik_ctx* c, eik_stats* stats) {
+    if (!c) return fail(nullptr, EIK_EINVAL, "eik_wait: ctx is NULL");
+    if (!c->in_flight) return fail(c, EIK_ESTATE, "eik_wait: no solve in flight");
+    c->in_flight = false;
+    EIK_CK(c, cudaStreamSynchronize(c->stream));
+    eikg::Ctrl H{};
+    EIK_CK(c, cudaMemcpy(&H, c->ctrl, sizeof(H), cudaMemcpyDeviceToHost));
+    c->host_ctrl = H;
+    c->last_nr = H.k;
+    eik_status st = EIK_OK;
+    if (H.status & (eikg::kStWaitTimeout | eikg::kStRestartCap | eikg::kStRoundCap)) {
+        st = EIK_ETIMEOUT;
+        c->err = std::string("solve stopped early: ") +
+                 ((H.status & eikg::kStRestartCap) ? "restart cap reached " : "") +
+                 ((H.status & eikg::kStWaitTimeout) ? "grid-barrier wait limit reached " : "") +
+                 ((H.status & eikg::kStRoundCap) ? "march round cap reached" : "");
+    } else if (!H.done) {
+        st = EIK_ECUDA;
+        c->err = "solve did not finish";
+    }
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->restarts = H.k;
+        stats->marches = static_cast<int64_t>(H.marches);
+        stats->accepted = static_cast<int64_t>(H.accepted);
+        stats->solves = static_cast<int64_t>(H.solves);
+        stats->updates = static_cast<int64_t>(H.updates);
+        stats->fallbacks = static_cast<int64_t>(H.fallbacks);
+        stats->rounds = static_cast<int64_t>(H.rounds);
+        stats->device_ms = (H.t_end > H.t_begin) ? static_cast<double>(H.t_end - H.t_begin) * 1e-6 : 0.0;
+        stats->final_bound = H.bound;
+        stats->status = st;
+        stats->block_dim = c->params.block_dim;
+    }
+    if (st == EIK_OK) c->solved = true;
+    return st;
+}
+
+eik_status eik_solve_ex(eik_ctx* c, const eik_params* params, eik_stats* stats) {
+    eik_status st = eik_solve_async(c, params);
+    if (st != EIK_OK) return st;
+    return eik_wait(c, stats);
+}
+
+eik_status eik_solve(eik_ctx* c, double stride, int32_t block_dim, eik_stats* stats) {
+    eik_params p;
+    eik_params_default(&p);
+    p.stride = stride;
+    p.block_dim = block_dim;
+    return eik_solve_ex(c, &p, stats);
+}
+
+eik_status eik_restart_log(eik_ctx* c, eik_restart_rec* out, int64_t cap, int64_t* n) {
+    if (!c) return fail(nullptr, EIK_EINVAL, "eik_restart_log: ctx is NULL");
+    if (!n || (cap > 0 && !out)) return fail(c, EIK_EINVAL, "eik_restart_log: NULL output");
+    if (c->in_flight) return fail(c, EIK_ESTATE, "eik_restart_log: a solve is in flight");
+    if (!c->params.log_restarts || !c->log) {
+        *n = 0;
+        return EIK_OK;
+    }
+    int64_t cnt = std::min<int64_t>(c->last_nr, c->log_cap);
+    cnt = std::min<int64_t>(cnt, cap);
+    static_assert(sizeof(eik_restart_rec) == sizeof(eikg::RestartRec), "record layout");
+    if (cnt > 0) EIK_CK(c, cudaMemcpy(out, c->log, sizeof(eik_restart_rec) * cnt, cudaMemcpyDeviceToHost));
+    *n = cnt;
+    return EIK_OK;
+}
+
+eik_status eik_result(eik_ctx* c, void* out, int out_on_device) {
+    if (!c) return fail(nullptr, EIK_EINVAL, "eik_result: ctx is NULL");
+    if (!out) return fail(c, EIK_EINVAL, "eik_result: psi_out is NULL");
+    if (c->in_flight) return fail(c, EIK_ESTATE, "eik_result: a solve is in flight (call eik_wait)");
+    if (!c->solved) return fail(c, EIK_ESTATE, "eik_result: no successful solve yet");
+    const size_t plane = static_cast<size_t>(c->nx) * c->ny * c->esz;
+    auto run = [&](void* dst, int z0, int z1) -> cudaError_t {
+        if (c->prec == EIK_FP32)
+            return eikg::launch_result<float>(static_cast<const float*>(c->slot), c->stamp, static_cast<float*>(dst),
+                                              c->nx, c->ny, z0, z1, c->BX, c->BY, c->stream);
+        return eikg::launch_result<double>(static_cast<const double*>(c->slot), c->stamp, static_cast<double*>(dst),
+                                           c->nx, c->ny, z0, z1, c->BX, c->BY, c->stream);
+    };
+    if (out_on_device) {
+        EIK_CK(c, run(out, 0, c->nz));
+        EIK_CK(c, cudaStreamSynchronize(c->stream));
+        return EIK_OK;
+    }
+    const size_t bytes = plane * c->nz;
+    if (bytes > c->fstage_cap) {
+        if (c->fstage) cudaFree(c->fstage);
+        c->fstage = nullptr;
+        c->fstage_cap = 0;
+        EIK_CK(c, cudaMalloc(&c->fstage, bytes));
+        c->fstage_cap = bytes;
+    }
+    EIK_CK(c, run(c->fstage, 0, c->nz));
+    EIK_CK(c, cudaMemcpyAsync(out, c->fstage, bytes, cudaMemcpyDeviceToHost, c->stream));
+    EIK_CK(c, cudaStreamSynchronize(c->stream));
+    return EIK_OK;
+}
+
+void eik_destroy(eik_ctx* c) {
+    if (!c) return;
+    if (c->in_flight) cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+}  // extern "C"

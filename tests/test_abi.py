@@ -1,0 +1,68 @@
+"""The C ABI library loads and exports every entry point include/eik.h declares (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for hdr in os.listdir(os.path.join(ROOT, "include")):
+        if not hdr.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:eik_status|void|const\s+char\s*\*)\s*\**\s*(eik_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def eik():
+    from paper_1811_00009_gb300 import build
+    build.build()
+    import paper_1811_00009_gb300 as E
+    return E
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("eik_create", "eik_add_sources", "eik_solve", "eik_result", "eik_destroy", "eik_last_error"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(eik):
+    L = eik.lib()
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_host_only_entry_points(eik):
+    assert "sm_103a" in eik.eik_version()
+    p = eik.eik_params_default()
+    assert p.block_dim == 8 and abs(p.window - 1 / np.sqrt(3)) < 1e-15 and p.fallback_tau == 0.125
+
+
+@pytest.mark.parametrize("dims,h", [((0, 4, 4), 0.1), ((4, 4, -1), 0.1), ((4, 4, 4), 0.0),
+                                    ((4, 4, 4), float("nan")), ((4, 4, 4), float("inf")),
+                                    ((2048, 2048, 1024), 0.1)])
+def test_create_rejects_bad_arguments_before_touching_the_device(eik, dims, h):
+    L = eik.lib()
+    out = C.c_void_p()
+    d = (C.c_int32 * 3)(*dims)
+    F = np.ones(8, np.float32)
+    st = L.eik_create(C.byref(out), d, h, C.c_void_p(F.ctypes.data), 0, 0, None)
+    assert st == eik.EIK_EINVAL
+    assert not out.value
+    assert eik.eik_last_error(None)
+
+
+def test_null_context_calls_fail_cleanly(eik):
+    L = eik.lib()
+    assert L.eik_solve(None, 1.0, 8, None) == eik.EIK_EINVAL
+    assert L.eik_result(None, None, 0) == eik.EIK_EINVAL
+    assert L.eik_add_sources(None, 0, None) == eik.EIK_EINVAL
+    L.eik_destroy(None)
