@@ -20,7 +20,8 @@
  *  - Alg. 3's quadratic a*x^2 - 2*b*x + c = 0 is evaluated on values
  *    measured from the smallest upwind value (the same root, without the
  *    cancellation of b^2 - a*c at large psi); a negative discriminant, which
- *    exact arithmetic never produces, is clamped to zero;
+ *    exact arithmetic never produces, is clamped to zero, and so is a root
+ *    below the largest admitted value (causality, see orc_solve_quadratic);
  *  - heap ties are broken by the point index;
  *  - barrier nodes (F = 0) are never solved (Sec. 3.3);
  *  - bound_band accumulates by repeated addition of the stride (Alg. 6).
@@ -158,6 +159,12 @@ double orc_solve_quadratic(double psi_c, const double nbv[6], const int nbk[6], 
         double disc = b * b - a * c;
         if (disc < 0.0) disc = 0.0;
         double t = v[0] + (b + sqrt(disc)) / a;
+        /* Causality of the upwind scheme (Sec. 2.1): the root is never below the
+         * largest admitted value.  The admission test of Alg. 3 guarantees this
+         * in exact arithmetic; rounding can break it by an ulp when the last
+         * admitted value sits right at the threshold, which would let two nodes
+         * lower each other endlessly.  Enforce it. */
+        if (t < v[id - 1]) t = v[id - 1];
         if (id < nd && t > v[id]) { ++id; continue; }
         return t;
     }
