@@ -199,6 +199,9 @@ def run_ours(args):
 
     stream = torch.cuda.current_stream()
     pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in pairs:                   # torch creates the CUDA event on first record; the library re-records it
+        a.record(stream)
+        b.record(stream)
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     if ws > 1:

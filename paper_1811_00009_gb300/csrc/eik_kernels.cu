@@ -76,17 +76,20 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
 // whose differences are exact.  Whenever a value is admitted D > r^2 in
 // exact arithmetic, so D < tau*k*r^2 (tau < 1/3) only flags rounding trouble.
 // ---------------------------------------------------------------------------
+// The root never falls below the largest admitted value (causality of the
+// upwind scheme; exact arithmetic guarantees it, rounding could break it by an
+// ulp and let two nodes lower each other forever), hence the fmax clamps.
 __device__ __forceinline__ double upwind_root(double a, double b, double c, double r) {
     double x = a + r;
     if (!(x > b)) return x;
     const double d = b - a;
     const double r2 = r * r;
     double D = 2.0 * r2 - d * d;
-    x = a + (d + sqrt(fmax(D, 0.0))) * 0.5;
+    x = fmax(a + (d + sqrt(fmax(D, 0.0))) * 0.5, b);
     if (!(x > c)) return x;
     const double e = c - a, g = c - b;
     D = 3.0 * r2 - (d * d + e * e + g * g);
-    return a + (d + e + sqrt(fmax(D, 0.0))) / 3.0;
+    return fmax(a + (d + e + sqrt(fmax(D, 0.0))) / 3.0, c);
 }
 
 __device__ __forceinline__ float upwind_root_f32(float a, float b, float c, float r, float tau, int& fb) {
@@ -99,7 +102,7 @@ __device__ __forceinline__ float upwind_root_f32(float a, float b, float c, floa
         ++fb;
         return static_cast<float>(upwind_root(a, b, c, r));
     }
-    x = a + (d + sqrtf(D)) * 0.5f;
+    x = fmaxf(a + (d + sqrtf(D)) * 0.5f, b);
     if (!(x > c)) return x;
     const float e = c - a, g = c - b;
     D = 3.0f * r2 - (d * d + e * e + g * g);
@@ -107,7 +110,7 @@ __device__ __forceinline__ float upwind_root_f32(float a, float b, float c, floa
         ++fb;
         return static_cast<float>(upwind_root(a, b, c, r));
     }
-    return a + (d + e + sqrtf(D)) / 3.0f;
+    return fmaxf(a + (d + e + sqrtf(D)) / 3.0f, c);
 }
 
 template <typename T>
@@ -413,7 +416,7 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
         }
         for (unsigned m = G; m; m &= m - 1) lmin = vmin(lmin, vabs(S.psi[ghost_halo(__ffs(m) - 1, y, z0)]));
         const T mn = warp_min(lmin);
-        if (!(static_cast<double>(mn) <= bound)) break;
+        if (!(mn < INF) || !(static_cast<double>(mn) <= bound)) break;   // band empty, or above the bound
         if (++rounds > kRoundCap) {
             atomicOr(&P.ctrl->status, kStRoundCap);
             break;
