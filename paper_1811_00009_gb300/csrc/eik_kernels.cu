@@ -113,6 +113,16 @@ __device__ __forceinline__ float upwind_root_f32(float a, float b, float c, floa
     return fmaxf(a + (d + e + sqrtf(D)) / 3.0f, c);
 }
 
+// Bounds arrive as doubles; a float node value v satisfies v <= b exactly when
+// v <= (the largest float <= b), so the FP32 path compares in float (FP64
+// throughput on this part is a small fraction of FP32).
+template <typename T>
+__device__ __forceinline__ T bound_down(double b);
+template <>
+__device__ __forceinline__ float bound_down<float>(double b) { return __double2float_rd(b); }
+template <>
+__device__ __forceinline__ double bound_down<double>(double b) { return b; }
+
 template <typename T>
 struct RootOf;
 template <>
@@ -255,9 +265,11 @@ __device__ __forceinline__ int ghost_halo(int bit, int y, int z0) {
 // Alg. 5 for its ghost layer done first from the neighbours' copies as of
 // the end of restart k-1.
 template <typename T>
-__device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, int k, double bprev,
-                            double bound, int lane, MarchAcc& acc) {
+__device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, int k, double bprev_d,
+                            double bound_d, int lane, MarchAcc& acc) {
     const T INF = Num<T>::inf();
+    const T bprev = bound_down<T>(bprev_d);
+    const T bound = bound_down<T>(bound_d);
     const int y = lane & 7, zp = lane >> 3, z0 = 2 * zp;
     const int BX = P.BX, BY = P.BY, BZ = P.BZ;
     const int bx = b % BX, by = (b / BX) % BY, bz = b / (BX * BY);
@@ -370,7 +382,7 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
     for (int j = 0; j < 16; ++j) {
         const int hh = hbase + (j >> 3) * 100 + (j & 7);
         const T v = S.psi[hh];
-        if (v < INF && static_cast<double>(v) > bprev) {
+        if (v < INF && v > bprev) {
             B |= 1u << j;
             S.psi[hh] = -v;
         }
@@ -378,7 +390,7 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
     auto mark_ghost = [&](int bit, unsigned long long um, int uu) {
         const int hh = ghost_halo(bit, y, z0);
         const T g = S.psi[hh];
-        if (g < INF && (((um >> uu) & 1ull) || static_cast<double>(g) > bprev)) {
+        if (g < INF && (((um >> uu) & 1ull) || g > bprev)) {
             G |= 1u << bit;
             S.psi[hh] = -g;
         }
@@ -402,7 +414,7 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
     const T rmin_b = warp_min(rlo);
     acc.rmin = fminf(acc.rmin, static_cast<float>(rmin_b));
     acc.rmax = fmaxf(acc.rmax, static_cast<float>(warp_max(rhi)));
-    const double w = P.window * static_cast<double>(rmin_b);
+    const T w = static_cast<T>(P.window * static_cast<double>(rmin_b));
     const float tau = static_cast<float>(P.fallback_tau);
 
     // ---- rounds of windowed ordered acceptance
@@ -416,18 +428,18 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
         }
         for (unsigned m = G; m; m &= m - 1) lmin = vmin(lmin, vabs(S.psi[ghost_halo(__ffs(m) - 1, y, z0)]));
         const T mn = warp_min(lmin);
-        if (!(mn < INF) || !(static_cast<double>(mn) <= bound)) break;   // band empty, or above the bound
+        if (!(mn < INF) || !(mn <= bound)) break;   // band empty, or above the bound
         if (++rounds > kRoundCap) {
             atomicOr(&P.ctrl->status, kStRoundCap);
             break;
         }
-        const double thr = fmin(static_cast<double>(mn) + w, bound);
+        const T thr = vmin(mn + w, bound);
         unsigned A = 0, AG = 0;
         for (unsigned m = B; m; m &= m - 1) {
             const int j = __ffs(m) - 1;
             const int hh = hbase + (j >> 3) * 100 + (j & 7);
             const T v = vabs(S.psi[hh]);
-            if (static_cast<double>(v) <= thr) {
+            if (v <= thr) {
                 A |= 1u << j;
                 S.psi[hh] = v;
             }
@@ -436,7 +448,7 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
             const int bit = __ffs(m) - 1;
             const int hh = ghost_halo(bit, y, z0);
             const T v = vabs(S.psi[hh]);
-            if (static_cast<double>(v) <= thr) {
+            if (v <= thr) {
                 AG |= 1u << bit;
                 S.psi[hh] = v;
             }
@@ -668,7 +680,7 @@ __device__ bool end_of_restart(const LoopParams<T>& P) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kWarps * 32) k_restart_loop(LoopParams<T> P) {
+__global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<T>& S = reinterpret_cast<WarpSmem<T>*>(smem_raw)[warp];
