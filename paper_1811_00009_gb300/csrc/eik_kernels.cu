@@ -139,12 +139,17 @@ struct RootOf<double> {
 };
 
 // Per-warp shared memory.
+constexpr int kBandCap = 896;      // 512 interior + 384 ghost nodes: every node at most once
+
 template <typename T>
 struct __align__(16) WarpSmem {
-    T psi[1000];          // brick plus one ghost layer, index ((z+1)*10 + (y+1))*10 + (x+1)
-    T r[kBrick];          // h/F, brick index
-    uint16_t list[kBrick];
-    uint8_t newp[kBrick]; // nodes lowered in the current round (byte flags)
+    T psi[1000];            // brick plus one ghost layer, index ((z+1)*10 + (y+1))*10 + (x+1)
+    T r[kBrick];            // h/F, brick index
+    uint16_t band[kBandCap];// the narrow band: halo indices of the pending nodes
+    uint16_t list[kBrick];  // nodes to re-solve in the current round (brick index)
+    uint32_t dirty[16];     // bit per brick node: neighbour of a node accepted this round
+    uint32_t upd[16];       // bit per brick node: lowered in this march (Upsilon)
+    uint32_t fxob[16];      // bit per brick node: fixed, barrier or padding node (never solved)
 };
 
 __device__ __forceinline__ int halo_of(int p) {
@@ -232,13 +237,9 @@ __device__ __forceinline__ unsigned long long warp_or64(unsigned long long v) {
     const unsigned hi = __reduce_or_sync(kFull, static_cast<unsigned>(v >> 32));
     return (static_cast<unsigned long long>(hi) << 32) | lo;
 }
-// eight 0/1 bytes -> eight bits (byte i -> bit i)
-__device__ __forceinline__ unsigned pack_bytes(unsigned long long x) {
-    return static_cast<unsigned>((x * 0x0102040810204080ull) >> 56);
-}
 
 struct MarchAcc {
-    unsigned accepted, band;                 // per lane
+    unsigned accepted, band;                 // counted on lane 0
     int fallbacks;                           // per lane
     unsigned long long solves, updates, rounds;  // the same on every lane
     float rmin, rmax;                        // the same on every lane
@@ -409,74 +410,101 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
 #pragma unroll
         for (int x = 0; x < 8; ++x) mark_ghost(20 + x, um, y * 8 + x);
     }
+    if (lane < 16) {
+        S.dirty[lane] = 0u;
+        S.upd[lane] = 0u;
+        S.fxob[lane] = 0u;
+    }
     __syncwarp();
+    if (FXOB & 0xFFu) atomicOr(&S.fxob[pbase >> 5], (FXOB & 0xFFu) << (pbase & 31));
+    if (FXOB >> 8) atomicOr(&S.fxob[(pbase + 64) >> 5], (FXOB >> 8) << ((pbase + 64) & 31));
 
     const T rmin_b = warp_min(rlo);
     acc.rmin = fminf(acc.rmin, static_cast<float>(rmin_b));
     acc.rmax = fmaxf(acc.rmax, static_cast<float>(warp_max(rhi)));
     const T w = static_cast<T>(P.window * static_cast<double>(rmin_b));
     const float tau = static_cast<float>(P.fallback_tau);
+    const unsigned lt = (1u << lane) - 1u;
 
-    // ---- rounds of windowed ordered acceptance
-    unsigned U = 0;                   // own nodes lowered in this march
+    // ---- the band as a list shared by the warp (one entry per pending node)
+    int n;
+    {
+        const int cnt = __popc(B) + __popc(G);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        n = __shfl_sync(kFull, incl, 31);
+        int off = incl - cnt;
+        for (unsigned m = B; m; m &= m - 1) {
+            const int j = __ffs(m) - 1;
+            S.band[off++] = static_cast<uint16_t>(hbase + (j >> 3) * 100 + (j & 7));
+        }
+        for (unsigned m = G; m; m &= m - 1) S.band[off++] = static_cast<uint16_t>(ghost_halo(__ffs(m) - 1, y, z0));
+    }
+    __syncwarp();
+
+    // ---- rounds of windowed ordered acceptance (Alg. 4)
     int rounds = 0;
     for (;;) {
         T lmin = INF;
-        for (unsigned m = B; m; m &= m - 1) {
-            const int j = __ffs(m) - 1;
-            lmin = vmin(lmin, vabs(S.psi[hbase + (j >> 3) * 100 + (j & 7)]));
-        }
-        for (unsigned m = G; m; m &= m - 1) lmin = vmin(lmin, vabs(S.psi[ghost_halo(__ffs(m) - 1, y, z0)]));
+        for (int i = lane; i < n; i += 32) lmin = vmin(lmin, vabs(S.psi[S.band[i]]));
         const T mn = warp_min(lmin);
-        if (!(mn < INF) || !(mn <= bound)) break;   // band empty, or above the bound
+        if (!(mn < INF) || !(mn <= bound)) break;   // band empty, or its minimum above the bound
         if (++rounds > kRoundCap) {
             atomicOr(&P.ctrl->status, kStRoundCap);
             break;
         }
         const T thr = vmin(mn + w, bound);
-        unsigned A = 0, AG = 0;
-        for (unsigned m = B; m; m &= m - 1) {
-            const int j = __ffs(m) - 1;
-            const int hh = hbase + (j >> 3) * 100 + (j & 7);
-            const T v = vabs(S.psi[hh]);
-            if (v <= thr) {
-                A |= 1u << j;
-                S.psi[hh] = v;
+        // accept (Remove_Min of a window), keep the rest of the band in order,
+        // and mark the accepted nodes' neighbours inside the brick (Alg. 2)
+        int kept = 0;
+        for (int base = 0; base < n; base += 32) {
+            const int i = base + lane;
+            int hh = 0;
+            bool keep = false, take = false;
+            if (i < n) {
+                hh = S.band[i];
+                const T v = vabs(S.psi[hh]);
+                if (v <= thr) {
+                    take = true;
+                    S.psi[hh] = v;
+                } else {
+                    keep = true;
+                }
+            }
+            const unsigned km = __ballot_sync(kFull, keep);
+            const unsigned tm = __ballot_sync(kFull, take);
+            if (keep) S.band[kept + __popc(km & lt)] = static_cast<uint16_t>(hh);
+            kept += __popc(km);
+            if (lane == 0) acc.accepted += __popc(tm);
+            if (take) {
+                const int px = hh % 10 - 1, py = (hh / 10) % 10 - 1, pz = hh / 100 - 1;
+                auto cand = [&](int x, int yy, int z) {
+                    if (static_cast<unsigned>(x) < 8u && static_cast<unsigned>(yy) < 8u && static_cast<unsigned>(z) < 8u) {
+                        const int q = (z * 8 + yy) * 8 + x;
+                        atomicOr(&S.dirty[q >> 5], 1u << (q & 31));
+                    }
+                };
+                cand(px - 1, py, pz);
+                cand(px + 1, py, pz);
+                cand(px, py - 1, pz);
+                cand(px, py + 1, pz);
+                cand(px, py, pz - 1);
+                cand(px, py, pz + 1);
             }
         }
-        for (unsigned m = G; m; m &= m - 1) {
-            const int bit = __ffs(m) - 1;
-            const int hh = ghost_halo(bit, y, z0);
-            const T v = vabs(S.psi[hh]);
-            if (v <= thr) {
-                AG |= 1u << bit;
-                S.psi[hh] = v;
-            }
-        }
-        B &= ~A;
-        G &= ~AG;
-        acc.accepted += __popc(A) + __popc(AG);
+        n = kept;
         __syncwarp();
 
-        // Alg. 2: neighbours of the accepted nodes inside the brick
-        unsigned D = ((A << 1) & 0xFEFEu) | ((A >> 1) & 0x7F7Fu);   // x +- 1
-        D |= ((A & 0xFFu) << 8) | (A >> 8);                          // z0 <-> z1 in this lane
-        const unsigned zup = __shfl_down_sync(kFull, A, 8);          // lane with z + 2
-        const unsigned zdn = __shfl_up_sync(kFull, A, 8);            // lane with z - 2
-        if (zp < 3) D |= (zup & 0xFFu) << 8;
-        if (zp > 0) D |= zdn >> 8;
-        const unsigned yup = __shfl_down_sync(kFull, A, 1);          // lane with y + 1
-        const unsigned ydn = __shfl_up_sync(kFull, A, 1);            // lane with y - 1
-        if (y < 7) D |= yup;
-        if (y > 0) D |= ydn;
-        D |= (AG & 1u) | ((AG & 2u) << 7) | ((AG & 4u) << 5) | ((AG & 8u) << 12);
-        D |= (AG >> 4) & 0xFFFFu;
-        if (zp == 0) D |= (AG >> 20) & 0xFFu;
-        if (zp == 3) D |= ((AG >> 20) & 0xFFu) << 8;
-        D &= ~FXOB & 0xFFFFu;
-
-        // compaction of the nodes to re-solve
-        const int cnt = __popc(D);
+        // candidates -> list of nodes to re-solve; never-solved nodes dropped
+        const unsigned word = S.dirty[lane >> 1] & ~S.fxob[lane >> 1];
+        const unsigned wd = (lane & 1) ? (word >> 16) : (word & 0xFFFFu);
+        __syncwarp();
+        if (lane < 16) S.dirty[lane] = 0u;
+        const int cnt = __popc(wd);
         int incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -485,23 +513,23 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
         }
         const int total = __shfl_sync(kFull, incl, 31);
         int off = incl - cnt;
-        for (unsigned m = D; m; m &= m - 1) {
-            const int j = __ffs(m) - 1;
-            S.list[off++] = static_cast<uint16_t>(pbase + (j >> 3) * 64 + (j & 7));
-        }
+        for (unsigned m = wd; m; m &= m - 1)
+            S.list[off++] = static_cast<uint16_t>((lane >> 1) * 32 + (lane & 1) * 16 + __ffs(m) - 1);
         __syncwarp();
         acc.solves += total;
 
         // Alg. 3 for each listed node, 32 at a time; new values land after the reads
         for (int base = 0; base < total; base += 32) {
             const int idx = base + lane;
-            bool imp = false;
+            bool imp = false, known = false;
             T xn = 0;
             int hq = 0, q = 0;
             if (idx < total) {
                 q = S.list[idx];
                 hq = halo_of(q);
-                const T c = vabs(S.psi[hq]);
+                const T cur = S.psi[hq];
+                const T c = vabs(cur);
+                known = !sgn(cur);
                 // KNOWN neighbours below the node's current value (Alg. 3's test)
                 auto kn = [&](T v) -> T { return (sgn(v) || !(v < c)) ? INF : v; };
                 T mx = vmin(kn(S.psi[hq - 1]), kn(S.psi[hq + 1]));
@@ -518,31 +546,24 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
                 }
             }
             __syncwarp();
+            // a lowered node is tagged BAND (Alg. 2): it joins the band unless already in it
+            const bool add = imp && known;
+            const unsigned am = __ballot_sync(kFull, add);
             if (imp) {
                 S.psi[hq] = -xn;
-                S.newp[q] = 1;
+                atomicOr(&S.upd[q >> 5], 1u << (q & 31));
             }
+            if (add) S.band[n + __popc(am & lt)] = static_cast<uint16_t>(hq);
+            n += __popc(am);
             acc.updates += __popc(__ballot_sync(kFull, imp));
             __syncwarp();
         }
-
-        // lowered own nodes rejoin the band (Alg. 2: tag BAND)
-        {
-            unsigned long long* np = reinterpret_cast<unsigned long long*>(S.newp);
-            const unsigned long long n0 = np[pbase >> 3], n1 = np[(pbase + 64) >> 3];
-            if (n0 | n1) {
-                const unsigned nb = pack_bytes(n0) | (pack_bytes(n1) << 8);
-                B |= nb;
-                U |= nb;
-                np[pbase >> 3] = 0;
-                np[(pbase + 64) >> 3] = 0;
-            }
-        }
-        __syncwarp();
     }
     acc.rounds += rounds;
 
     // ---- Upsilon: own face nodes lowered in this march, per face (face-local bit masks)
+    const unsigned U = ((S.upd[pbase >> 5] >> (pbase & 31)) & 0xFFu) |
+                       (((S.upd[(pbase + 64) >> 5] >> ((pbase + 64) & 31)) & 0xFFu) << 8);
     unsigned long long um[6];
     um[0] = (static_cast<unsigned long long>(U & 1u) << (z0 * 8 + y)) |
             (static_cast<unsigned long long>((U >> 8) & 1u) << ((z0 + 1) * 8 + y));
@@ -576,7 +597,7 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
     if (lane == 0) P.stamp[b] = (k << 1) | ns;
 
     // ---- activation for restart k+1 (A of Alg. 4/5, C of Alg. 4)
-    const bool pending = __any_sync(kFull, (B | G) != 0u);
+    const bool pending = n > 0;
     int32_t* next = ((k + 1) & 1) ? P.list1 : P.list0;
     auto enqueue = [&](int32_t x) {
         if (atomicMax(P.queued + x, k + 1) < k + 1) {
@@ -586,7 +607,7 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
     };
     if (lane == 0 && pending) enqueue(b);
     if (lane < 6 && um[lane] != 0ull && nbr[lane] >= 0) enqueue(nbr[lane]);
-    acc.band += __popc(B) + __popc(G);
+    if (lane == 0) acc.band += n;
 }
 
 // Grid barrier at the end of restart k.  The CTA arriving last does the
@@ -684,8 +705,6 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<T>& S = reinterpret_cast<WarpSmem<T>*>(smem_raw)[warp];
-    for (int i = lane; i < kBrick / 8; i += 32) reinterpret_cast<unsigned long long*>(S.newp)[i] = 0ull;
-    __syncwarp();
     Ctrl* C = P.ctrl;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const unsigned long long t0 = globaltimer();
