@@ -7,10 +7,12 @@
 //   slot[b][2][640]     two copies of the brick's psi: 512 interior values,
 //                       then its x = 0 and x = 7 faces (64 each, index z*8+y)
 //                       stored contiguously for the neighbours' ghost reads
-//   slot_k[b][2]        restart that wrote each copy (-1: never)
 //   ups[b][2][6]        per copy, the 64-bit mask of face nodes lowered in the
 //                       march that wrote it (Upsilon of Alg. 2/4), per face
-//   stamp[b]            (restart << 1) | copy of the latest state, -1 untouched
+//   stamp[b]            64 bits: restart that wrote the latest copy (high 32),
+//                       restart that wrote the other copy (bits 31..1, all ones
+//                       if never), index of the latest copy (bit 0); all ones
+//                       for a brick no march has touched
 //   queued[b]           last restart the brick was put on the work list for
 // A march at restart k reads the brick's latest copy and its neighbours' copies
 // as of the end of restart k-1, and writes the other copy, so no warp ever
@@ -29,6 +31,18 @@ constexpr int kSlot = 640;         // values per brick copy
 constexpr int kXF0 = 512;          // offset of the x = 0 face inside a copy
 constexpr int kXF7 = 576;          // offset of the x = 7 face
 constexpr int kWarps = 8;          // warps per CTA of the restart loop (one brick per warp)
+
+constexpr unsigned long long kUntouched = ~0ull;   // stamp of a brick no march has written
+constexpr unsigned kNever = 0x7fffffffu;           // "other copy never written"
+
+__host__ __device__ inline int stamp_latest(unsigned long long w) { return static_cast<int>(w >> 32); }
+__host__ __device__ inline int stamp_other(unsigned long long w) { return static_cast<int>((w >> 1) & kNever); }
+__host__ __device__ inline int stamp_copy(unsigned long long w) { return static_cast<int>(w & 1ull); }
+__host__ __device__ inline unsigned long long make_stamp(int latest, int other, int copy) {
+    return (static_cast<unsigned long long>(static_cast<unsigned>(latest)) << 32) |
+           (static_cast<unsigned long long>(static_cast<unsigned>(other) & kNever) << 1) |
+           static_cast<unsigned long long>(copy & 1);
+}
 
 // status bits of a device run
 constexpr int kStWaitTimeout = 1;  // a grid-barrier wait ran out of iterations
@@ -77,9 +91,8 @@ struct LoopParams {
     int32_t BX, BY, BZ;
     int64_t nbricks;
     T* slot;
-    int32_t* slot_k;
     unsigned long long* ups;
-    int32_t* stamp;
+    unsigned long long* stamp;
     int32_t* queued;
     const T* rr;
     int32_t* list0;

@@ -277,24 +277,20 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
     const int pbase = (z0 * 8 + y) * 8;                          // brick index of (0, y, z0)
     const int hbase = ((z0 + 1) * 10 + (y + 1)) * 10 + 1;       // halo index of (0, y, z0)
 
-    // ---- own state: the latest copy, or +inf for an untouched brick
-    const int32_t st = __ldcg(P.stamp + b);
-    {
-        T row[8];
-        if (st < 0) {
+    // ---- load phase 1 (independent loads): stamps of the brick and its six
+    // neighbours, and h/F of this lane's two rows
+    const unsigned long long st = __ldcg(P.stamp + b);
+    int nbr[6];
+    nbr[0] = bx > 0 ? b - 1 : -1;
+    nbr[1] = bx < BX - 1 ? b + 1 : -1;
+    nbr[2] = by > 0 ? b - BX : -1;
+    nbr[3] = by < BY - 1 ? b + BX : -1;
+    nbr[4] = bz > 0 ? b - BX * BY : -1;
+    nbr[5] = bz < BZ - 1 ? b + BX * BY : -1;
+    unsigned long long wst[6];
 #pragma unroll
-            for (int x = 0; x < 8; ++x) S.psi[hbase + x] = INF, S.psi[hbase + 100 + x] = INF;
-        } else {
-            const T* src = P.slot + (static_cast<int64_t>(b) * 2 + (st & 1)) * kSlot;
-            load8_cg(src + pbase, row);
-#pragma unroll
-            for (int x = 0; x < 8; ++x) S.psi[hbase + x] = row[x];
-            load8_cg(src + pbase + 64, row);
-#pragma unroll
-            for (int x = 0; x < 8; ++x) S.psi[hbase + 100 + x] = row[x];
-        }
-    }
-    // ---- h/F: fixed nodes (r < 0) and barrier/padding nodes (r = +inf) are never solved
+    for (int f = 0; f < 6; ++f) wst[f] = nbr[f] >= 0 ? __ldcg(P.stamp + nbr[f]) : kUntouched;
+    // fixed nodes (r < 0) and barrier/padding nodes (r = +inf) are never solved
     unsigned FXOB = 0;
     T rlo = INF, rhi = 0;
     {
@@ -315,39 +311,35 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
             }
         }
     }
-    // ---- ghost layer: neighbours' faces as of the end of restart k-1 (Alg. 5)
-    int nbr[6];
-    nbr[0] = bx > 0 ? b - 1 : -1;
-    nbr[1] = bx < BX - 1 ? b + 1 : -1;
-    nbr[2] = by > 0 ? b - BX : -1;
-    nbr[3] = by < BY - 1 ? b + BX : -1;
-    nbr[4] = bz > 0 ? b - BX * BY : -1;
-    nbr[5] = bz < BZ - 1 ? b + BX * BY : -1;
+    // ---- load phase 2: the brick's latest copy, and the ghost layer: the
+    // neighbours' faces as of the end of restart k-1 with their Upsilon masks
+    // (Alg. 5).  A neighbour that already marched in this restart is read from
+    // its other copy.
+    int fsl[6];
     unsigned long long fups[6];
+    T fv0[6], fv1[6];
+    const int u = 2 * lane;                                       // face-local index of this lane's pair
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
-        const int nb = nbr[f];
-        int sl = -1;
-        unsigned long long um = 0;
-        if (nb >= 0) {
-            const int32_t w = __ldcg(P.stamp + nb);
-            if (w >= 0) {
-                sl = w & 1;
-                int32_t written = w >> 1;
-                if (written >= k) {                               // already marched in this restart
-                    sl ^= 1;
-                    written = __ldcg(P.slot_k + 2 * nb + sl);
-                    if (written < 0) sl = -1;
-                }
-                if (sl >= 0 && written == k - 1)
-                    um = __ldcg(P.ups + (static_cast<int64_t>(nb) * 2 + sl) * 6 + (f ^ 1));
+        const unsigned long long w = wst[f];
+        int sl = -1, written = -1;
+        if (w != kUntouched) {
+            if (stamp_latest(w) >= k) {
+                written = stamp_other(w);
+                sl = (written == static_cast<int>(kNever)) ? -1 : (stamp_copy(w) ^ 1);
+            } else {
+                written = stamp_latest(w);
+                sl = stamp_copy(w);
             }
         }
-        fups[f] = um;
-        const int u = 2 * lane;                                   // face-local index of this lane's pair
-        T v0 = INF, v1 = INF;
+        fsl[f] = sl;
+        fups[f] = (sl >= 0 && written == k - 1)
+                      ? __ldcg(P.ups + (static_cast<int64_t>(nbr[f]) * 2 + sl) * 6 + (f ^ 1))
+                      : 0ull;
+        fv0[f] = INF;
+        fv1[f] = INF;
         if (sl >= 0) {
-            const T* src = P.slot + (static_cast<int64_t>(nb) * 2 + sl) * kSlot;
+            const T* src = P.slot + (static_cast<int64_t>(nbr[f]) * 2 + sl) * kSlot;
             int off;
             if (f == 0) off = kXF7 + u;
             else if (f == 1) off = kXF0 + u;
@@ -355,8 +347,25 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
             else if (f == 3) off = ((u >> 3) * 8 + 0) * 8 + (u & 7);
             else if (f == 4) off = 7 * 64 + u;
             else off = u;
-            load2_cg(src + off, v0, v1);
+            load2_cg(src + off, fv0[f], fv1[f]);
         }
+    }
+    {
+        T row[8];
+        if (st == kUntouched) {
+#pragma unroll
+            for (int x = 0; x < 8; ++x) S.psi[hbase + x] = INF, S.psi[hbase + 100 + x] = INF;
+        } else {
+            const T* src = P.slot + (static_cast<int64_t>(b) * 2 + stamp_copy(st)) * kSlot;
+            T row1[8];
+            load8_cg(src + pbase, row);
+            load8_cg(src + pbase + 64, row1);
+#pragma unroll
+            for (int x = 0; x < 8; ++x) S.psi[hbase + x] = row[x], S.psi[hbase + 100 + x] = row1[x];
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
         int h0, step;
         if (f < 2) {
             const int yy = u & 7, zz = u >> 3;
@@ -371,8 +380,8 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
             h0 = ((f == 4 ? 0 : 9) * 10 + (yy + 1)) * 10 + (xx + 1);
             step = 1;
         }
-        S.psi[h0] = v0;
-        S.psi[h0 + step] = v1;
+        S.psi[h0] = fv0[f];
+        S.psi[h0 + step] = fv1[f];
     }
     __syncwarp();
 
@@ -577,7 +586,7 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
     for (int f = 0; f < 6; ++f) um[f] = warp_or64(um[f]);
 
     // ---- write the other copy, then publish it
-    const int ns = (st < 0) ? 0 : ((st & 1) ^ 1);
+    const int ns = (st == kUntouched) ? 0 : (stamp_copy(st) ^ 1);
     T* dst = P.slot + (static_cast<int64_t>(b) * 2 + ns) * kSlot;
     {
         T row[8];
@@ -591,10 +600,10 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
         }
     }
     if (lane < 6) P.ups[(static_cast<int64_t>(b) * 2 + ns) * 6 + lane] = um[lane];
-    if (lane == 0) P.slot_k[2 * b + ns] = k;
-    __threadfence();
-    __syncwarp();
-    if (lane == 0) P.stamp[b] = (k << 1) | ns;
+    // No fence: nobody reads this copy before the grid barrier that ends the
+    // restart (a reader that sees the new stamp takes the other copy).
+    if (lane == 0)
+        P.stamp[b] = make_stamp(k, st == kUntouched ? static_cast<int>(kNever) : stamp_latest(st), ns);
 
     // ---- activation for restart k+1 (A of Alg. 4/5, C of Alg. 4)
     const bool pending = n > 0;
@@ -776,8 +785,8 @@ __global__ void k_layout_speed(const T* __restrict__ F, T* __restrict__ rr, int 
 template <typename T>
 __global__ void k_init_sources(int nfix, const int32_t* __restrict__ fix_b, const int32_t* __restrict__ fix_p,
                                const double* __restrict__ fix_v, int nsrcb, const int32_t* __restrict__ src_bricks,
-                               int nenq, const int32_t* __restrict__ enq, T* slot, int32_t* slot_k,
-                               unsigned long long* ups, int32_t* stamp, int32_t* queued, T* rr, T* saved_r,
+                               int nenq, const int32_t* __restrict__ enq, T* slot, unsigned long long* ups,
+                               unsigned long long* stamp, int32_t* queued, T* rr, T* saved_r,
                                int32_t* list1) {
     const T INF = Num<T>::inf();
     if (blockIdx.x < nsrcb) {
@@ -795,10 +804,7 @@ __global__ void k_init_sources(int nfix, const int32_t* __restrict__ fix_b, cons
             if (x == 7) dst[kXF7 + z * 8 + y] = v;
         }
         if (threadIdx.x < 6) ups[static_cast<int64_t>(b) * 2 * 6 + threadIdx.x] = 0ull;
-        if (threadIdx.x == 0) {
-            slot_k[2 * b] = 0;
-            stamp[b] = 0;
-        }
+        if (threadIdx.x == 0) stamp[b] = make_stamp(0, static_cast<int>(kNever), 0);   // "restart 0", copy 0
     } else {
         const int base = (blockIdx.x - nsrcb) * blockDim.x + threadIdx.x;
         if (base < nfix) {
@@ -830,7 +836,7 @@ __global__ void k_gather_r(int n, const int32_t* __restrict__ nb_b, const int32_
 
 // Latest copy of every brick -> psi in x-fastest order, nodes z in [z_begin, z_end).
 template <typename T>
-__global__ void k_result(const T* __restrict__ slot, const int32_t* __restrict__ stamp, T* __restrict__ out, int nx,
+__global__ void k_result(const T* __restrict__ slot, const unsigned long long* __restrict__ stamp, T* __restrict__ out, int nx,
                          int ny, int z_begin, int z_end, int BX, int BY) {
     const T INF = Num<T>::inf();
     const int64_t plane = static_cast<int64_t>(nx) * ny;
@@ -842,8 +848,8 @@ __global__ void k_result(const T* __restrict__ slot, const int32_t* __restrict__
         const int j = static_cast<int>(rem / nx), i = static_cast<int>(rem % nx);
         const int64_t b = (static_cast<int64_t>(k >> 3) * BY + (j >> 3)) * BX + (i >> 3);
         const int p = ((k & 7) * 8 + (j & 7)) * 8 + (i & 7);
-        const int32_t st = stamp[b];
-        out[t] = (st < 0) ? INF : slot[(b * 2 + (st & 1)) * kSlot + p];
+        const unsigned long long st = stamp[b];
+        out[t] = (st == kUntouched) ? INF : slot[(b * 2 + stamp_copy(st)) * kSlot + p];
     }
 }
 
@@ -863,12 +869,12 @@ cudaError_t launch_layout_speed(const T* F, T* rr, int nx, int ny, int nz, int B
 template <typename T>
 cudaError_t launch_init_sources(int nfix, const int32_t* fix_b, const int32_t* fix_p, const double* fix_v,
                                 int nsrcb, const int32_t* src_bricks, int nenq, const int32_t* enq, T* slot,
-                                int32_t* slot_k, unsigned long long* ups, int32_t* stamp, int32_t* queued, T* rr,
+                                unsigned long long* ups, unsigned long long* stamp, int32_t* queued, T* rr,
                                 T* saved_r, int32_t* list1, cudaStream_t s) {
     const int m = nfix > nenq ? nfix : nenq;
     const int grid = nsrcb + (m + 255) / 256;
-    k_init_sources<T><<<grid, 256, 0, s>>>(nfix, fix_b, fix_p, fix_v, nsrcb, src_bricks, nenq, enq, slot, slot_k,
-                                           ups, stamp, queued, rr, saved_r, list1);
+    k_init_sources<T><<<grid, 256, 0, s>>>(nfix, fix_b, fix_p, fix_v, nsrcb, src_bricks, nenq, enq, slot, ups,
+                                           stamp, queued, rr, saved_r, list1);
     return cudaGetLastError();
 }
 
@@ -889,7 +895,7 @@ cudaError_t launch_gather_r(int n, const int32_t* nb_b, const int32_t* nb_p, con
 }
 
 template <typename T>
-cudaError_t launch_result(const T* slot, const int32_t* stamp, T* out, int nx, int ny, int z_begin, int z_end,
+cudaError_t launch_result(const T* slot, const unsigned long long* stamp, T* out, int nx, int ny, int z_begin, int z_end,
                           int BX, int BY, cudaStream_t s) {
     const int64_t total = static_cast<int64_t>(nx) * ny * (z_end - z_begin);
     int grid = static_cast<int>((total + 255) / 256);
@@ -925,13 +931,12 @@ cudaError_t launch_restart_loop(const LoopParams<T>& P, int grid, cudaStream_t s
     template cudaError_t launch_layout_speed<T>(const T*, T*, int, int, int, int, int, int64_t, double, int*,    \
                                                 cudaStream_t);                                                   \
     template cudaError_t launch_init_sources<T>(int, const int32_t*, const int32_t*, const double*, int,         \
-                                                const int32_t*, int, const int32_t*, T*, int32_t*,                \
-                                                unsigned long long*, int32_t*, int32_t*, T*, T*, int32_t*,        \
-                                                cudaStream_t);                                                   \
+                                                const int32_t*, int, const int32_t*, T*, unsigned long long*,     \
+                                                unsigned long long*, int32_t*, T*, T*, int32_t*, cudaStream_t);    \
     template cudaError_t launch_restore_r<T>(int, const int32_t*, const int32_t*, const T*, T*, cudaStream_t);   \
     template cudaError_t launch_gather_r<T>(int, const int32_t*, const int32_t*, const T*, double*,              \
                                             cudaStream_t);                                                       \
-    template cudaError_t launch_result<T>(const T*, const int32_t*, T*, int, int, int, int, int, int,            \
+    template cudaError_t launch_result<T>(const T*, const unsigned long long*, T*, int, int, int, int, int, int, \
                                           cudaStream_t);                                                         \
     template size_t loop_smem_bytes<T>();                                                                        \
     template cudaError_t loop_occupancy<T>(int*);                                                                \

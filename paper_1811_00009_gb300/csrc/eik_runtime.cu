@@ -21,14 +21,14 @@ template <typename T>
 cudaError_t launch_layout_speed(const T*, T*, int, int, int, int, int, int64_t, double, int*, cudaStream_t);
 template <typename T>
 cudaError_t launch_init_sources(int, const int32_t*, const int32_t*, const double*, int, const int32_t*, int,
-                                const int32_t*, T*, int32_t*, unsigned long long*, int32_t*, int32_t*, T*, T*,
+                                const int32_t*, T*, unsigned long long*, unsigned long long*, int32_t*, T*, T*,
                                 int32_t*, cudaStream_t);
 template <typename T>
 cudaError_t launch_restore_r(int, const int32_t*, const int32_t*, const T*, T*, cudaStream_t);
 template <typename T>
 cudaError_t launch_gather_r(int, const int32_t*, const int32_t*, const T*, double*, cudaStream_t);
 template <typename T>
-cudaError_t launch_result(const T*, const int32_t*, T*, int, int, int, int, int, int, cudaStream_t);
+cudaError_t launch_result(const T*, const unsigned long long*, T*, int, int, int, int, int, int, cudaStream_t);
 template <typename T>
 size_t loop_smem_bytes();
 template <typename T>
@@ -50,9 +50,8 @@ struct eik_ctx {
     size_t esz = 4;
     void* rr = nullptr;
     void* slot = nullptr;
-    int32_t* slot_k = nullptr;
     unsigned long long* ups = nullptr;
-    int32_t* stamp = nullptr;
+    unsigned long long* stamp = nullptr;
     int32_t* queued = nullptr;
     int32_t* list0 = nullptr;
     int32_t* list1 = nullptr;
@@ -103,7 +102,7 @@ cudaError_t dalloc(P** p, size_t bytes) {
 }
 
 void free_all(eik_ctx* c) {
-    void* ptrs[] = {c->rr,    c->slot,  c->slot_k, c->ups,   c->stamp,   c->queued, c->list0, c->list1,
+    void* ptrs[] = {c->rr,    c->slot,  c->ups,   c->stamp,   c->queued, c->list0, c->list1,
                     c->ctrl,  c->err_flag, c->log, c->scratch, c->fstage};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -210,9 +209,8 @@ eik_status eik_create(eik_ctx** out, const int32_t dims[3], double h, const void
     } allocs[] = {
         {&c->rr, nb * kBrick * c->esz},
         {&c->slot, nb * 2 * kSlot * c->esz},
-        {reinterpret_cast<void**>(&c->slot_k), nb * 2 * sizeof(int32_t)},
         {reinterpret_cast<void**>(&c->ups), nb * 2 * 6 * sizeof(unsigned long long)},
-        {reinterpret_cast<void**>(&c->stamp), nb * sizeof(int32_t)},
+        {reinterpret_cast<void**>(&c->stamp), nb * sizeof(unsigned long long)},
         {reinterpret_cast<void**>(&c->queued), nb * sizeof(int32_t)},
         {reinterpret_cast<void**>(&c->list0), nb * sizeof(int32_t)},
         {reinterpret_cast<void**>(&c->list1), nb * sizeof(int32_t)},
@@ -412,13 +410,12 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
     }
     // ---- Alg. 1 for every brick: untouched (psi = +inf) unless it holds fixed nodes
     const size_t nb = static_cast<size_t>(c->nbricks);
-    EIK_CK(c, cudaMemsetAsync(c->stamp, 0xFF, nb * sizeof(int32_t), s));
+    EIK_CK(c, cudaMemsetAsync(c->stamp, 0xFF, nb * sizeof(unsigned long long), s));
     EIK_CK(c, cudaMemsetAsync(c->queued, 0xFF, nb * sizeof(int32_t), s));
-    EIK_CK(c, cudaMemsetAsync(c->slot_k, 0xFF, nb * 2 * sizeof(int32_t), s));
     if (nfix > 0)
         EIK_CK(c, eikg::launch_init_sources<T>(nfix, c->d_fix_b, c->d_fix_p, d_fv, static_cast<int>(sb.size()), d_sb,
                                                static_cast<int>(enq.size()), d_enq, static_cast<T*>(c->slot),
-                                               c->slot_k, c->ups, c->stamp, c->queued, static_cast<T*>(c->rr),
+                                               c->ups, c->stamp, c->queued, static_cast<T*>(c->rr),
                                                static_cast<T*>(c->d_saved_r), c->list1, s));
     // ---- control block: restart 1 with bound_1 = 0 + stride
     eikg::Ctrl& H = c->host_ctrl;
@@ -451,7 +448,6 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
         L.BZ = c->BZ;
         L.nbricks = c->nbricks;
         L.slot = static_cast<T*>(c->slot);
-        L.slot_k = c->slot_k;
         L.ups = c->ups;
         L.stamp = c->stamp;
         L.queued = c->queued;
