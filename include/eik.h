@@ -102,7 +102,7 @@ typedef struct {
     int32_t schedule;       /* eik_schedule */
     double window;          /* acceptance window factor omega: each march round accepts every band
                                point within omega * h / F_max(block) of the band minimum
-                               (0 = default 1/sqrt(3)) */
+                               (0 = default 2; 1/sqrt(3) is the smallest increment of Alg. 3) */
     double fallback_tau;    /* FP32 mode: fall back to double when D < tau * k * (h/F)^2 (0 = default 1/8) */
     int64_t max_restarts;   /* restart cap (0 = default 1 << 24); reaching it returns EIK_ETIMEOUT */
     int32_t log_restarts;   /* non-zero: record per-restart statistics (eik_restart_log) */

@@ -155,7 +155,7 @@ void eik_params_default(eik_params* p) {
     p->stride = 0.0;
     p->block_dim = 8;
     p->schedule = EIK_SCHED_FIXED;
-    p->window = 1.0 / std::sqrt(3.0);
+    p->window = 2.0;
     p->fallback_tau = 0.125;
     p->max_restarts = int64_t(1) << 24;
     p->log_restarts = 0;
@@ -499,7 +499,7 @@ eik_status eik_solve_async(eik_ctx* c, const eik_params* params) {
     eik_params P = *params;
     if (P.block_dim == 0) P.block_dim = 8;
     if (P.max_restarts == 0) P.max_restarts = int64_t(1) << 24;
-    if (P.window == 0.0) P.window = 1.0 / std::sqrt(3.0);
+    if (P.window == 0.0) P.window = 2.0;
     c->params = P;
     st = (c->prec == EIK_FP32) ? queue_solve<float>(c, P) : queue_solve<double>(c, P);
     if (st != EIK_OK) return st;

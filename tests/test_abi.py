@@ -43,7 +43,7 @@ def test_every_declared_symbol_is_exported(eik):
 def test_host_only_entry_points(eik):
     assert "sm_103a" in eik.eik_version()
     p = eik.eik_params_default()
-    assert p.block_dim == 8 and abs(p.window - 1 / np.sqrt(3)) < 1e-15 and p.fallback_tau == 0.125
+    assert p.block_dim == 8 and p.window == 2.0 and p.fallback_tau == 0.125
 
 
 @pytest.mark.parametrize("dims,h", [((0, 4, 4), 0.1), ((4, 4, -1), 0.1), ((4, 4, 4), 0.0),
