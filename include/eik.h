@@ -183,6 +183,45 @@ const char *eik_last_error(const eik_ctx *ctx);
 /* eik_version -- library version string. */
 const char *eik_version(void);
 
+/*
+ * eik_solve_noalloc -- one complete solve that allocates no device memory.
+ *
+ * No counterpart in the paper: this is a deployment entry point.  It serves
+ * callers that cannot call cudaMalloc at solve time -- code that lives under
+ * a memory pool or caching allocator it does not own, code that runs inside
+ * a CUDA stream capture, and embedders that must keep the process's device
+ * footprint fixed.  All working memory of the solve lives in one fixed device
+ * array inside the library (EIK_NOALLOC_SCRATCH_BYTES, 64 MiB), which every
+ * GPU that loads the library holds until the process exits.
+ *
+ *   dims, h   grid as in eik_create; the grid's 8x8x8 bricks,
+ *             ceil(nx/8)*ceil(ny/8)*ceil(nz/8), must not exceed
+ *             EIK_NOALLOC_MAX_BRICKS (e.g. 160^3 or 128x128x256 fit).
+ *   F         nx*ny*nz float speeds in DEVICE memory (x fastest), finite, >= 0.
+ *   nsrc, xyz 1..EIK_NOALLOC_MAX_SOURCES point sources, host memory, as in
+ *             eik_add_sources.
+ *   params    nullable (defaults); stride must be > 0; fixed schedule, 8^3 blocks.
+ *   psi_out   nx*ny*nz floats in DEVICE memory: the solution (FP32 mode only).
+ *   stats     nullable.
+ *   stream    cudaStream_t or NULL.  The call returns after the solve finished.
+ * Errors: EIK_EINVAL for a grid above the limit (with a message saying so),
+ * bad arguments or bad F; eik_noalloc_last_error() describes the failure.
+ *
+ * The array's device address is looked up on the first call made with a
+ * given device current: make that first call before any stream capture.
+ * Every call shares the array and leaves its contents behind; each call
+ * clears what must start empty.  Calls that overlap on the GPU (from two host
+ * threads, or on two streams) race on the array and must not be issued.
+ */
+#define EIK_NOALLOC_SCRATCH_BYTES (64u << 20)
+#define EIK_NOALLOC_MAX_BRICKS 8192
+#define EIK_NOALLOC_MAX_SOURCES 64
+eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float *F, int32_t nsrc, const double *xyz,
+                             const eik_params *params, float *psi_out, eik_stats *stats, void *stream);
+
+/* eik_noalloc_last_error -- message of the calling thread's last failed eik_solve_noalloc. */
+const char *eik_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif
