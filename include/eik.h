@@ -98,7 +98,8 @@ typedef enum {
 
 typedef struct {
     double stride;          /* bound increment in psi units (> 0; +inf = the naive block method) */
-    int32_t block_dim;      /* block edge in nodes: 8 (0 = default 8) */
+    int32_t block_dim;      /* block edge in nodes: 8 (one warp per block) or 16 (one CTA per block of
+                               2x2x2 bricks); 0 = default 8 */
     int32_t schedule;       /* eik_schedule */
     double window;          /* acceptance window factor omega: each march round accepts every band
                                point within omega * h / F_max(block) of the band minimum
@@ -145,7 +146,7 @@ void eik_params_default(eik_params *p);
 /*
  * eik_solve -- run the method (Alg. 6) with a fixed stride and wait for it.
  *   stride     > 0, may be +inf.
- *   block_dim  8, or 0 for the default.
+ *   block_dim  8 or 16, or 0 for the default (8).
  *   stats      nullable.
  * Returns EIK_ESTATE if no source was added, EIK_ETIMEOUT if the restart cap
  * or a device wait limit was hit.

@@ -14,6 +14,7 @@
 //                       if never), index of the latest copy (bit 0); all ones
 //                       for a brick no march has touched
 //   queued[b]           last restart the brick was put on the work list for
+//   qgroup[g]           the same for the group g of 2x2x2 bricks (16^3 blocks)
 // A march at restart k reads the brick's latest copy and its neighbours' copies
 // as of the end of restart k-1, and writes the other copy, so no warp ever
 // reads memory written during the same restart: the exchange step of Alg. 5
@@ -57,8 +58,11 @@ struct Ctrl {
     int32_t k;                 // current restart (1-based)
     int32_t done;
     int32_t status;
-    int32_t count[2];          // work-list lengths, by restart parity
-    int32_t head[2];           // next work-list entry to hand out
+    int32_t count[2];          // brick work-list lengths, by restart parity
+    int32_t head[2];           // next brick work-list entry to hand out
+    int32_t gcount[2];         // group (16^3 block) work-list lengths, by restart parity
+    int32_t ghead[2];          // next group work-list entry to hand out
+    int32_t mode;              // block edge of restart k: 8 (one warp per brick) or 16 (one CTA per group)
     int32_t pad0;
     double bound;              // bound_band of restart k
     double bound_prev;         // bound_band of restart k-1 (-1 at k = 1)
@@ -97,6 +101,11 @@ struct LoopParams {
     const T* rr;
     int32_t* list0;
     int32_t* list1;
+    int32_t GX, GY, GZ;        // groups of 2x2x2 bricks per axis
+    int32_t groups;            // non-zero: keep the group work lists (16^3 restarts possible)
+    int32_t* qgroup;           // per group: last restart it was put on the group list for
+    int32_t* glist0;
+    int32_t* glist1;
     Ctrl* ctrl;
     RestartRec* log;
     int64_t log_cap;
@@ -105,7 +114,7 @@ struct LoopParams {
     int64_t max_restarts;
     long long wait_limit;      // spin iterations before a barrier wait gives up
     int32_t sched;             // 0 fixed, 1 learned
-    int32_t pad;
+    int32_t mode_fixed;        // block edge of every restart under the fixed schedule (8 or 16)
     const float* mlp;          // schedule network weights (learned schedule)
     double h;
 };

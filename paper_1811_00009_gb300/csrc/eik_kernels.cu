@@ -262,182 +262,204 @@ __device__ __forceinline__ int ghost_halo(int bit, int y, int z0) {
     return (plane * 10 + (y + 1)) * 10 + (x + 1);
 }
 
-// March_Narrow_Band (Alg. 4) of brick b at restart k, with the exchange of
-// Alg. 5 for its ghost layer done first from the neighbours' copies as of
-// the end of restart k-1.
+// Face-local element u of face f (x faces: u = z*8+y, y faces: u = z*8+x,
+// z faces: u = y*8+x): halo index of the ghost node beyond face f, and halo
+// index of the brick's own boundary node on face f.
+__device__ __forceinline__ int face_ghost_halo(int f, int u) {
+    const int a = u & 7, c = u >> 3;
+    if (f < 2) return ((c + 1) * 10 + (a + 1)) * 10 + (f == 0 ? 0 : 9);
+    if (f < 4) return ((c + 1) * 10 + (f == 2 ? 0 : 9)) * 10 + (a + 1);
+    return ((f == 4 ? 0 : 9) * 10 + (c + 1)) * 10 + (a + 1);
+}
+__device__ __forceinline__ int face_own_halo(int f, int u) {
+    const int a = u & 7, c = u >> 3;
+    if (f < 2) return ((c + 1) * 10 + (a + 1)) * 10 + (f == 0 ? 1 : 8);
+    if (f < 4) return ((c + 1) * 10 + (f == 2 ? 1 : 8)) * 10 + (a + 1);
+    return ((f == 4 ? 1 : 8) * 10 + (c + 1)) * 10 + (a + 1);
+}
+
+// Put brick x (and, if the block work list is kept, its block) on restart
+// k+1's work lists, once per restart (the "queued" marks dedupe).
 template <typename T>
-__device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, int k, double bprev_d,
-                            double bound_d, int lane, MarchAcc& acc) {
+__device__ __forceinline__ void enqueue_next(const LoopParams<T>& P, int k, int32_t x) {
+    const int par = (k + 1) & 1;
+    if (atomicMax(P.queued + x, k + 1) < k + 1) {
+        const int pos = atomicAdd(&P.ctrl->count[par], 1);
+        (par ? P.list1 : P.list0)[pos] = x;
+    }
+    if (!P.groups) return;
+    const int bx = x % P.BX, by = (x / P.BX) % P.BY, bz = x / (P.BX * P.BY);
+    const int32_t g = ((bz >> 1) * P.GY + (by >> 1)) * P.GX + (bx >> 1);
+    if (atomicMax(P.qgroup + g, k + 1) < k + 1) {
+        const int pos = atomicAdd(&P.ctrl->gcount[par], 1);
+        (par ? P.glist1 : P.glist0)[pos] = g;
+    }
+}
+
+// March_Narrow_Band (Alg. 4) of brick b at restart k, with the exchange of
+// Alg. 5 for its ghost layer done first from the neighbours' copies as of the
+// end of restart k-1.
+//
+// GROUP = false: one warp, one 8^3 block.  GROUP = true: the eight warps of the
+// CTA march the 2x2x2 bricks of one 16^3 block together (warp w holds brick
+// (w & 1, (w >> 1) & 1, w >> 2) of the group; b < 0 for a brick outside the
+// grid, whose warp only takes part in the barriers).  The rounds then share
+// one acceptance threshold, an accepted node marks the neighbouring warp's
+// nodes across internal faces, and after every phase each warp refreshes its
+// ghost layer on internal faces from the neighbouring warp's tile, so
+// information crosses the internal faces within the restart as it does inside
+// one block of the paper.
+template <typename T, bool GROUP>
+__device__ void march(const LoopParams<T>& P, WarpSmem<T>* SW, int warp, int32_t b, unsigned gmask, int k,
+                      double bprev_d, double bound_d, int lane, MarchAcc& acc) {
+    __shared__ double s_wmin[kWarps];
+    WarpSmem<T>& S = SW[warp];
     const T INF = Num<T>::inf();
     const T bprev = bound_down<T>(bprev_d);
     const T bound = bound_down<T>(bound_d);
+    const bool present = b >= 0;
     const int y = lane & 7, zp = lane >> 3, z0 = 2 * zp;
     const int BX = P.BX, BY = P.BY, BZ = P.BZ;
-    const int bx = b % BX, by = (b / BX) % BY, bz = b / (BX * BY);
+    const int bb = present ? b : 0;
+    const int bx = bb % BX, by = (bb / BX) % BY, bz = bb / (BX * BY);
     const int pbase = (z0 * 8 + y) * 8;                          // brick index of (0, y, z0)
     const int hbase = ((z0 + 1) * 10 + (y + 1)) * 10 + 1;       // halo index of (0, y, z0)
+    const unsigned lt = (1u << lane) - 1u;
 
-    // ---- load phase 1 (independent loads): stamps of the brick and its six
-    // neighbours, and h/F of this lane's two rows
-    const unsigned long long st = __ldcg(P.stamp + b);
     int nbr[6];
-    nbr[0] = bx > 0 ? b - 1 : -1;
-    nbr[1] = bx < BX - 1 ? b + 1 : -1;
-    nbr[2] = by > 0 ? b - BX : -1;
-    nbr[3] = by < BY - 1 ? b + BX : -1;
-    nbr[4] = bz > 0 ? b - BX * BY : -1;
-    nbr[5] = bz < BZ - 1 ? b + BX * BY : -1;
-    unsigned long long wst[6];
-#pragma unroll
-    for (int f = 0; f < 6; ++f) wst[f] = nbr[f] >= 0 ? __ldcg(P.stamp + nbr[f]) : kUntouched;
-    // fixed nodes (r < 0) and barrier/padding nodes (r = +inf) are never solved
-    unsigned FXOB = 0;
+    nbr[0] = bx > 0 ? bb - 1 : -1;
+    nbr[1] = bx < BX - 1 ? bb + 1 : -1;
+    nbr[2] = by > 0 ? bb - BX : -1;
+    nbr[3] = by < BY - 1 ? bb + BX : -1;
+    nbr[4] = bz > 0 ? bb - BX * BY : -1;
+    nbr[5] = bz < BZ - 1 ? bb + BX * BY : -1;
+
+    unsigned long long st = kUntouched;
+    unsigned FXOB = 0xFFFFu;
     T rlo = INF, rhi = 0;
-    {
-        T row[8];
-        const T* rs = P.rr + static_cast<int64_t>(b) * kBrick;
+    int n = 0;
+    if (present) {
+        // ---- load phase 1 (independent loads): stamps of the brick and its six
+        // neighbours, and h/F of this lane's two rows
+        st = __ldcg(P.stamp + b);
+        unsigned long long wst[6];
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            load8_ro(rs + pbase + 64 * s, row);
-            store8(S.r + pbase + 64 * s, row);
+        for (int f = 0; f < 6; ++f) wst[f] = nbr[f] >= 0 ? __ldcg(P.stamp + nbr[f]) : kUntouched;
+        // fixed nodes (r < 0) and barrier/padding nodes (r = +inf) are never solved
+        FXOB = 0;
+        {
+            T row[8];
+            const T* rs = P.rr + static_cast<int64_t>(b) * kBrick;
 #pragma unroll
-            for (int x = 0; x < 8; ++x) {
-                const T r = row[x];
-                if (!(r > 0) || !(r < INF)) FXOB |= 1u << (8 * s + x);
-                else {
-                    rlo = vmin(rlo, r);
-                    rhi = vmax(rhi, r);
+            for (int s = 0; s < 2; ++s) {
+                load8_ro(rs + pbase + 64 * s, row);
+                store8(S.r + pbase + 64 * s, row);
+#pragma unroll
+                for (int x = 0; x < 8; ++x) {
+                    const T r = row[x];
+                    if (!(r > 0) || !(r < INF)) FXOB |= 1u << (8 * s + x);
+                    else {
+                        rlo = vmin(rlo, r);
+                        rhi = vmax(rhi, r);
+                    }
                 }
             }
         }
-    }
-    // ---- load phase 2: the brick's latest copy, and the ghost layer: the
-    // neighbours' faces as of the end of restart k-1 with their Upsilon masks
-    // (Alg. 5).  A neighbour that already marched in this restart is read from
-    // its other copy.
-    int fsl[6];
-    unsigned long long fups[6];
-    T fv0[6], fv1[6];
-    const int u = 2 * lane;                                       // face-local index of this lane's pair
+        // ---- load phase 2: the brick's latest copy, and the ghost layer: the
+        // neighbours' faces as of the end of restart k-1 with their Upsilon masks
+        // (Alg. 5).  A neighbour that already marched in this restart is read from
+        // its other copy.
+        unsigned long long fups[6];
+        T fv0[6], fv1[6];
+        const int u = 2 * lane;                                   // face-local index of this lane's pair
 #pragma unroll
-    for (int f = 0; f < 6; ++f) {
-        const unsigned long long w = wst[f];
-        int sl = -1, written = -1;
-        if (w != kUntouched) {
-            if (stamp_latest(w) >= k) {
-                written = stamp_other(w);
-                sl = (written == static_cast<int>(kNever)) ? -1 : (stamp_copy(w) ^ 1);
-            } else {
-                written = stamp_latest(w);
-                sl = stamp_copy(w);
+        for (int f = 0; f < 6; ++f) {
+            const unsigned long long w = wst[f];
+            int sl = -1, written = -1;
+            if (w != kUntouched) {
+                if (stamp_latest(w) >= k) {
+                    written = stamp_other(w);
+                    sl = (written == static_cast<int>(kNever)) ? -1 : (stamp_copy(w) ^ 1);
+                } else {
+                    written = stamp_latest(w);
+                    sl = stamp_copy(w);
+                }
+            }
+            fups[f] = (sl >= 0 && written == k - 1)
+                          ? __ldcg(P.ups + (static_cast<int64_t>(nbr[f]) * 2 + sl) * 6 + (f ^ 1))
+                          : 0ull;
+            fv0[f] = INF;
+            fv1[f] = INF;
+            if (sl >= 0) {
+                const T* src = P.slot + (static_cast<int64_t>(nbr[f]) * 2 + sl) * kSlot;
+                int off;
+                if (f == 0) off = kXF7 + u;
+                else if (f == 1) off = kXF0 + u;
+                else if (f == 2) off = ((u >> 3) * 8 + 7) * 8 + (u & 7);
+                else if (f == 3) off = ((u >> 3) * 8 + 0) * 8 + (u & 7);
+                else if (f == 4) off = 7 * 64 + u;
+                else off = u;
+                load2_cg(src + off, fv0[f], fv1[f]);
             }
         }
-        fsl[f] = sl;
-        fups[f] = (sl >= 0 && written == k - 1)
-                      ? __ldcg(P.ups + (static_cast<int64_t>(nbr[f]) * 2 + sl) * 6 + (f ^ 1))
-                      : 0ull;
-        fv0[f] = INF;
-        fv1[f] = INF;
-        if (sl >= 0) {
-            const T* src = P.slot + (static_cast<int64_t>(nbr[f]) * 2 + sl) * kSlot;
-            int off;
-            if (f == 0) off = kXF7 + u;
-            else if (f == 1) off = kXF0 + u;
-            else if (f == 2) off = ((u >> 3) * 8 + 7) * 8 + (u & 7);
-            else if (f == 3) off = ((u >> 3) * 8 + 0) * 8 + (u & 7);
-            else if (f == 4) off = 7 * 64 + u;
-            else off = u;
-            load2_cg(src + off, fv0[f], fv1[f]);
-        }
-    }
-    {
-        T row[8];
-        if (st == kUntouched) {
+        {
+            T row[8];
+            if (st == kUntouched) {
 #pragma unroll
-            for (int x = 0; x < 8; ++x) S.psi[hbase + x] = INF, S.psi[hbase + 100 + x] = INF;
-        } else {
-            const T* src = P.slot + (static_cast<int64_t>(b) * 2 + stamp_copy(st)) * kSlot;
-            T row1[8];
-            load8_cg(src + pbase, row);
-            load8_cg(src + pbase + 64, row1);
+                for (int x = 0; x < 8; ++x) S.psi[hbase + x] = INF, S.psi[hbase + 100 + x] = INF;
+            } else {
+                const T* src = P.slot + (static_cast<int64_t>(b) * 2 + stamp_copy(st)) * kSlot;
+                T row1[8];
+                load8_cg(src + pbase, row);
+                load8_cg(src + pbase + 64, row1);
 #pragma unroll
-            for (int x = 0; x < 8; ++x) S.psi[hbase + x] = row[x], S.psi[hbase + 100 + x] = row1[x];
+                for (int x = 0; x < 8; ++x) S.psi[hbase + x] = row[x], S.psi[hbase + 100 + x] = row1[x];
+            }
         }
-    }
 #pragma unroll
-    for (int f = 0; f < 6; ++f) {
-        int h0, step;
-        if (f < 2) {
-            const int yy = u & 7, zz = u >> 3;
-            h0 = ((zz + 1) * 10 + (yy + 1)) * 10 + (f == 0 ? 0 : 9);
-            step = 10;
-        } else if (f < 4) {
-            const int xx = u & 7, zz = u >> 3;
-            h0 = ((zz + 1) * 10 + (f == 2 ? 0 : 9)) * 10 + (xx + 1);
-            step = 1;
-        } else {
-            const int xx = u & 7, yy = u >> 3;
-            h0 = ((f == 4 ? 0 : 9) * 10 + (yy + 1)) * 10 + (xx + 1);
-            step = 1;
+        for (int f = 0; f < 6; ++f) {
+            const int h0 = face_ghost_halo(f, u);
+            S.psi[h0] = fv0[f];
+            S.psi[h0 + (f < 2 ? 10 : 1)] = fv1[f];
         }
-        S.psi[h0] = fv0[f];
-        S.psi[h0 + step] = fv1[f];
-    }
-    __syncwarp();
+        __syncwarp();
 
-    // ---- the band at the start of the march: finite nodes above the previous
-    // bound, plus ghost nodes the neighbour lowered in restart k-1 (Upsilon)
-    unsigned B = 0, G = 0;
+        // ---- the band at the start of the march: finite nodes above the previous
+        // bound, plus ghost nodes the neighbour lowered in restart k-1 (Upsilon)
+        unsigned B = 0, G = 0;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        const int hh = hbase + (j >> 3) * 100 + (j & 7);
-        const T v = S.psi[hh];
-        if (v < INF && v > bprev) {
-            B |= 1u << j;
-            S.psi[hh] = -v;
+        for (int j = 0; j < 16; ++j) {
+            const int hh = hbase + (j >> 3) * 100 + (j & 7);
+            const T v = S.psi[hh];
+            if (v < INF && v > bprev) {
+                B |= 1u << j;
+                S.psi[hh] = -v;
+            }
         }
-    }
-    auto mark_ghost = [&](int bit, unsigned long long um, int uu) {
-        const int hh = ghost_halo(bit, y, z0);
-        const T g = S.psi[hh];
-        if (g < INF && (((um >> uu) & 1ull) || g > bprev)) {
-            G |= 1u << bit;
-            S.psi[hh] = -g;
+        auto mark_ghost = [&](int bit, unsigned long long um, int uu) {
+            const int hh = ghost_halo(bit, y, z0);
+            const T g = S.psi[hh];
+            if (g < INF && (((um >> uu) & 1ull) || g > bprev)) {
+                G |= 1u << bit;
+                S.psi[hh] = -g;
+            }
+        };
+        mark_ghost(0, fups[0], z0 * 8 + y);
+        mark_ghost(1, fups[0], (z0 + 1) * 8 + y);
+        mark_ghost(2, fups[1], z0 * 8 + y);
+        mark_ghost(3, fups[1], (z0 + 1) * 8 + y);
+        if (y == 0 || y == 7) {
+            const unsigned long long um = (y == 0) ? fups[2] : fups[3];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) mark_ghost(4 + j, um, (z0 + (j >> 3)) * 8 + (j & 7));
         }
-    };
-    mark_ghost(0, fups[0], z0 * 8 + y);
-    mark_ghost(1, fups[0], (z0 + 1) * 8 + y);
-    mark_ghost(2, fups[1], z0 * 8 + y);
-    mark_ghost(3, fups[1], (z0 + 1) * 8 + y);
-    if (y == 0 || y == 7) {
-        const unsigned long long um = (y == 0) ? fups[2] : fups[3];
+        if (zp == 0 || zp == 3) {
+            const unsigned long long um = (zp == 0) ? fups[4] : fups[5];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) mark_ghost(4 + j, um, (z0 + (j >> 3)) * 8 + (j & 7));
-    }
-    if (zp == 0 || zp == 3) {
-        const unsigned long long um = (zp == 0) ? fups[4] : fups[5];
-#pragma unroll
-        for (int x = 0; x < 8; ++x) mark_ghost(20 + x, um, y * 8 + x);
-    }
-    if (lane < 16) {
-        S.dirty[lane] = 0u;
-        S.upd[lane] = 0u;
-        S.fxob[lane] = 0u;
-    }
-    __syncwarp();
-    if (FXOB & 0xFFu) atomicOr(&S.fxob[pbase >> 5], (FXOB & 0xFFu) << (pbase & 31));
-    if (FXOB >> 8) atomicOr(&S.fxob[(pbase + 64) >> 5], (FXOB >> 8) << ((pbase + 64) & 31));
-
-    const T rmin_b = warp_min(rlo);
-    acc.rmin = fminf(acc.rmin, static_cast<float>(rmin_b));
-    acc.rmax = fmaxf(acc.rmax, static_cast<float>(warp_max(rhi)));
-    const T w = static_cast<T>(P.window * static_cast<double>(rmin_b));
-    const float tau = static_cast<float>(P.fallback_tau);
-    const unsigned lt = (1u << lane) - 1u;
-
-    // ---- the band as a list shared by the warp (one entry per pending node)
-    int n;
-    {
+            for (int x = 0; x < 8; ++x) mark_ghost(20 + x, um, y * 8 + x);
+        }
+        __syncwarp();
+        // ---- the band as a list shared by the warp (one entry per pending node)
         const int cnt = __popc(B) + __popc(G);
         int incl = cnt;
 #pragma unroll
@@ -453,14 +475,67 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
         }
         for (unsigned m = G; m; m &= m - 1) S.band[off++] = static_cast<uint16_t>(ghost_halo(__ffs(m) - 1, y, z0));
     }
+    if (lane < 16) {
+        S.dirty[lane] = 0u;
+        S.upd[lane] = 0u;
+        S.fxob[lane] = 0u;
+    }
     __syncwarp();
+    if (FXOB & 0xFFu) atomicOr(&S.fxob[pbase >> 5], (FXOB & 0xFFu) << (pbase & 31));
+    if (FXOB >> 8) atomicOr(&S.fxob[(pbase + 64) >> 5], (FXOB >> 8) << ((pbase + 64) & 31));
+
+    const T rmin_b = warp_min(rlo);
+    if (present) {
+        acc.rmin = fminf(acc.rmin, static_cast<float>(rmin_b));
+        acc.rmax = fmaxf(acc.rmax, static_cast<float>(warp_max(rhi)));
+    }
+    T w;
+    if constexpr (GROUP) {
+        // one window for the group: omega times the smallest h/F of its bricks
+        if (lane == 0) s_wmin[warp] = static_cast<double>(rmin_b);
+        __syncthreads();
+        double g = s_wmin[0];
+#pragma unroll
+        for (int i = 1; i < kWarps; ++i) g = fmin(g, s_wmin[i]);
+        w = static_cast<T>(P.window * g);
+        __syncthreads();
+    } else {
+        w = static_cast<T>(P.window * static_cast<double>(rmin_b));
+    }
+    const float tau = static_cast<float>(P.fallback_tau);
+
+    // ghost layer on internal faces <- the neighbouring warps' boundary nodes
+    auto refresh_internal = [&]() {
+        if constexpr (GROUP) {
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                if (!((gmask >> f) & 1u)) continue;
+                const WarpSmem<T>& NB = SW[warp ^ (1 << (f >> 1))];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int uu = 2 * lane + e;
+                    S.psi[face_ghost_halo(f, uu)] = NB.psi[face_own_halo(f ^ 1, uu)];
+                }
+            }
+            __syncwarp();
+        }
+    };
 
     // ---- rounds of windowed ordered acceptance (Alg. 4)
     int rounds = 0;
     for (;;) {
         T lmin = INF;
         for (int i = lane; i < n; i += 32) lmin = vmin(lmin, vabs(S.psi[S.band[i]]));
-        const T mn = warp_min(lmin);
+        T mn = warp_min(lmin);
+        if constexpr (GROUP) {
+            if (lane == 0) s_wmin[warp] = static_cast<double>(mn);
+            __syncthreads();
+            double g = s_wmin[0];
+#pragma unroll
+            for (int i = 1; i < kWarps; ++i) g = fmin(g, s_wmin[i]);
+            mn = static_cast<T>(g);
+            __syncthreads();
+        }
         if (!(mn < INF) || !(mn <= bound)) break;   // band empty, or its minimum above the bound
         if (++rounds > kRoundCap) {
             atomicOr(&P.ctrl->status, kStRoundCap);
@@ -468,7 +543,7 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
         }
         const T thr = vmin(mn + w, bound);
         // accept (Remove_Min of a window), keep the rest of the band in order,
-        // and mark the accepted nodes' neighbours inside the brick (Alg. 2)
+        // and mark the accepted nodes' neighbours (Alg. 2)
         int kept = 0;
         for (int base = 0; base < n; base += 32) {
             const int i = base + lane;
@@ -492,9 +567,21 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
             if (take) {
                 const int px = hh % 10 - 1, py = (hh / 10) % 10 - 1, pz = hh / 100 - 1;
                 auto cand = [&](int x, int yy, int z) {
-                    if (static_cast<unsigned>(x) < 8u && static_cast<unsigned>(yy) < 8u && static_cast<unsigned>(z) < 8u) {
+                    const bool ix = static_cast<unsigned>(x) < 8u, iy = static_cast<unsigned>(yy) < 8u,
+                               iz = static_cast<unsigned>(z) < 8u;
+                    if (ix && iy && iz) {
                         const int q = (z * 8 + yy) * 8 + x;
                         atomicOr(&S.dirty[q >> 5], 1u << (q & 31));
+                    } else if (GROUP) {
+                        // across an internal face: the neighbouring warp's node
+                        int f = -1;
+                        if (!ix && iy && iz) f = (x < 0) ? 0 : 1;
+                        else if (ix && !iy && iz) f = (yy < 0) ? 2 : 3;
+                        else if (ix && iy && !iz) f = (z < 0) ? 4 : 5;
+                        if (f >= 0 && ((gmask >> f) & 1u)) {
+                            const int q = (((z & 7) * 8) + (yy & 7)) * 8 + (x & 7);
+                            atomicOr(&SW[warp ^ (1 << (f >> 1))].dirty[q >> 5], 1u << (q & 31));
+                        }
                     }
                 };
                 cand(px - 1, py, pz);
@@ -506,7 +593,13 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
             }
         }
         n = kept;
-        __syncwarp();
+        if constexpr (GROUP) {
+            __syncthreads();
+            refresh_internal();
+            __syncthreads();
+        } else {
+            __syncwarp();
+        }
 
         // candidates -> list of nodes to re-solve; never-solved nodes dropped
         const unsigned word = S.dirty[lane >> 1] & ~S.fxob[lane >> 1];
@@ -567,10 +660,17 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
             acc.updates += __popc(__ballot_sync(kFull, imp));
             __syncwarp();
         }
+        if constexpr (GROUP) {
+            __syncthreads();
+            refresh_internal();
+        }
     }
     acc.rounds += rounds;
+    if constexpr (GROUP) __syncthreads();
+    if (!present) return;
 
-    // ---- Upsilon: own face nodes lowered in this march, per face (face-local bit masks)
+    // ---- Upsilon: own face nodes lowered in this march, per face (face-local bit
+    // masks); none on internal faces of a group, whose neighbours saw them live
     const unsigned U = ((S.upd[pbase >> 5] >> (pbase & 31)) & 0xFFu) |
                        (((S.upd[(pbase + 64) >> 5] >> ((pbase + 64) & 31)) & 0xFFu) << 8);
     unsigned long long um[6];
@@ -583,7 +683,10 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
     um[4] = (zp == 0) ? (static_cast<unsigned long long>(U & 0xFFu) << (y * 8)) : 0ull;
     um[5] = (zp == 3) ? (static_cast<unsigned long long>((U >> 8) & 0xFFu) << (y * 8)) : 0ull;
 #pragma unroll
-    for (int f = 0; f < 6; ++f) um[f] = warp_or64(um[f]);
+    for (int f = 0; f < 6; ++f) {
+        um[f] = warp_or64(um[f]);
+        if (GROUP && ((gmask >> f) & 1u)) um[f] = 0ull;
+    }
 
     // ---- write the other copy, then publish it
     const int ns = (st == kUntouched) ? 0 : (stamp_copy(st) ^ 1);
@@ -606,16 +709,8 @@ __device__ void march_brick(const LoopParams<T>& P, WarpSmem<T>& S, int32_t b, i
         P.stamp[b] = make_stamp(k, st == kUntouched ? static_cast<int>(kNever) : stamp_latest(st), ns);
 
     // ---- activation for restart k+1 (A of Alg. 4/5, C of Alg. 4)
-    const bool pending = n > 0;
-    int32_t* next = ((k + 1) & 1) ? P.list1 : P.list0;
-    auto enqueue = [&](int32_t x) {
-        if (atomicMax(P.queued + x, k + 1) < k + 1) {
-            const int pos = atomicAdd(&P.ctrl->count[(k + 1) & 1], 1);
-            next[pos] = x;
-        }
-    };
-    if (lane == 0 && pending) enqueue(b);
-    if (lane < 6 && um[lane] != 0ull && nbr[lane] >= 0) enqueue(nbr[lane]);
+    if (lane == 6 && n > 0) enqueue_next(P, k, b);
+    if (lane < 6 && um[lane] != 0ull && nbr[lane] >= 0) enqueue_next(P, k, nbr[lane]);
     if (lane == 0) acc.band += n;
 }
 
@@ -642,8 +737,10 @@ __device__ bool end_of_restart(const LoopParams<T>& P) {
             __threadfence();
             const int k = __ldcg(&C->k);
             const int par = k & 1;
-            const int n_this = __ldcg(&C->count[par]);
-            const int n_next = __ldcg(&C->count[par ^ 1]);
+            const int mode = __ldcg(&C->mode);
+            const int n_this = (mode == 16) ? __ldcg(&C->gcount[par]) : __ldcg(&C->count[par]);
+            const int next_mode = P.mode_fixed;
+            const int n_next = (next_mode == 16) ? __ldcg(&C->gcount[par ^ 1]) : __ldcg(&C->count[par ^ 1]);
             const unsigned long long now = globaltimer();
             const unsigned long long acc_a = __ldcg(&C->r_accepted), acc_band = __ldcg(&C->r_band);
             if (P.log != nullptr && k - 1 < P.log_cap) {
@@ -659,7 +756,7 @@ __device__ bool end_of_restart(const LoopParams<T>& P) {
                 rec.ms = static_cast<double>(now - __ldcg(&C->t_restart)) * 1e-6;
                 P.log[k - 1] = rec;
             }
-            C->marches += static_cast<unsigned long long>(n_this);
+            C->marches += static_cast<unsigned long long>(n_this) * (mode == 16 ? 8ull : 1ull);
             C->accepted += acc_a;
             C->solves += __ldcg(&C->r_solves);
             C->updates += __ldcg(&C->r_updates);
@@ -675,6 +772,8 @@ __device__ bool end_of_restart(const LoopParams<T>& P) {
             C->r_rmax_bits = 0u;
             C->count[par] = 0;
             C->head[par] = 0;
+            C->gcount[par] = 0;
+            C->ghead[par] = 0;
             if (n_next == 0) {
                 C->done = 1;
                 C->t_end = now;
@@ -686,6 +785,7 @@ __device__ bool end_of_restart(const LoopParams<T>& P) {
                 const double s = __ldcg(&C->stride);
                 const double bnd = __ldcg(&C->bound);
                 C->k = k + 1;
+                C->mode = next_mode;
                 C->bound_prev = bnd;
                 C->bound = bnd + s;                 // bound_band <- bound_band + stride (width = +inf)
                 C->t_restart = now;
@@ -712,8 +812,9 @@ __device__ bool end_of_restart(const LoopParams<T>& P) {
 template <typename T>
 __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpSmem<T>& S = reinterpret_cast<WarpSmem<T>*>(smem_raw)[warp];
+    WarpSmem<T>* SW = reinterpret_cast<WarpSmem<T>*>(smem_raw);
     Ctrl* C = P.ctrl;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const unsigned long long t0 = globaltimer();
@@ -724,18 +825,51 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P
         const int k = __ldcg(&C->k);
         const double bound = __ldcg(&C->bound);
         const double bprev = __ldcg(&C->bound_prev);
+        const int mode = __ldcg(&C->mode);
         const int par = k & 1;
-        const int n = __ldcg(&C->count[par]);
-        const int32_t* list = par ? P.list1 : P.list0;
         MarchAcc acc{0u, 0u, 0, 0ull, 0ull, 0ull, __int_as_float(0x7f800000), 0.0f};
         bool any = false;
-        for (;;) {
-            int i = 0;
-            if (lane == 0) i = atomicAdd(&C->head[par], 1);
-            i = __shfl_sync(kFull, i, 0);
-            if (i >= n) break;
-            march_brick<T>(P, S, __ldcg(list + i), k, bprev, bound, lane, acc);
-            any = true;
+        if (mode == 16) {
+            // one CTA per group of 2x2x2 bricks
+            const int n = __ldcg(&C->gcount[par]);
+            const int32_t* list = par ? P.glist1 : P.glist0;
+            for (;;) {
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    const int i = atomicAdd(&C->ghead[par], 1);
+                    s_item = (i < n) ? __ldcg(list + i) : -1;
+                }
+                __syncthreads();
+                const int g = s_item;
+                if (g < 0) break;
+                const int gx = g % P.GX, gy = (g / P.GX) % P.GY, gz = g / (P.GX * P.GY);
+                const int bx = 2 * gx + (warp & 1), by = 2 * gy + ((warp >> 1) & 1), bz = 2 * gz + (warp >> 2);
+                const bool in = bx < P.BX && by < P.BY && bz < P.BZ;
+                const int32_t b = in ? (bz * P.BY + by) * P.BX + bx : -1;
+                unsigned gmask = 0;
+                if (in) {
+                    if (warp & 1) gmask |= 1u;                     // -x neighbour in the group
+                    else if (bx + 1 < P.BX) gmask |= 2u;           // +x
+                    if (warp & 2) gmask |= 4u;
+                    else if (by + 1 < P.BY) gmask |= 8u;
+                    if (warp & 4) gmask |= 16u;
+                    else if (bz + 1 < P.BZ) gmask |= 32u;
+                }
+                march<T, true>(P, SW, warp, b, gmask, k, bprev, bound, lane, acc);
+                any = true;
+            }
+        } else {
+            // one warp per brick
+            const int n = __ldcg(&C->count[par]);
+            const int32_t* list = par ? P.list1 : P.list0;
+            for (;;) {
+                int i = 0;
+                if (lane == 0) i = atomicAdd(&C->head[par], 1);
+                i = __shfl_sync(kFull, i, 0);
+                if (i >= n) break;
+                march<T, false>(P, SW, warp, __ldcg(list + i), 0u, k, bprev, bound, lane, acc);
+                any = true;
+            }
         }
         if (any) {
             const unsigned acc_a = __reduce_add_sync(kFull, acc.accepted);
@@ -785,9 +919,9 @@ __global__ void k_layout_speed(const T* __restrict__ F, T* __restrict__ rr, int 
 template <typename T>
 __global__ void k_init_sources(int nfix, const int32_t* __restrict__ fix_b, const int32_t* __restrict__ fix_p,
                                const double* __restrict__ fix_v, int nsrcb, const int32_t* __restrict__ src_bricks,
-                               int nenq, const int32_t* __restrict__ enq, T* slot, unsigned long long* ups,
-                               unsigned long long* stamp, int32_t* queued, T* rr, T* saved_r,
-                               int32_t* list1) {
+                               int nenq, const int32_t* __restrict__ enq, int ngenq, const int32_t* __restrict__ genq,
+                               T* slot, unsigned long long* ups, unsigned long long* stamp, int32_t* queued,
+                               int32_t* qgroup, T* rr, T* saved_r, int32_t* list1, int32_t* glist1) {
     const T INF = Num<T>::inf();
     if (blockIdx.x < nsrcb) {
         const int32_t b = src_bricks[blockIdx.x];
@@ -815,6 +949,10 @@ __global__ void k_init_sources(int nfix, const int32_t* __restrict__ fix_b, cons
         if (base < nenq) {
             list1[base] = enq[base];
             queued[enq[base]] = 1;
+        }
+        if (base < ngenq) {
+            glist1[base] = genq[base];
+            qgroup[genq[base]] = 1;
         }
     }
 }
@@ -868,13 +1006,15 @@ cudaError_t launch_layout_speed(const T* F, T* rr, int nx, int ny, int nz, int B
 
 template <typename T>
 cudaError_t launch_init_sources(int nfix, const int32_t* fix_b, const int32_t* fix_p, const double* fix_v,
-                                int nsrcb, const int32_t* src_bricks, int nenq, const int32_t* enq, T* slot,
-                                unsigned long long* ups, unsigned long long* stamp, int32_t* queued, T* rr,
-                                T* saved_r, int32_t* list1, cudaStream_t s) {
-    const int m = nfix > nenq ? nfix : nenq;
+                                int nsrcb, const int32_t* src_bricks, int nenq, const int32_t* enq, int ngenq,
+                                const int32_t* genq, T* slot, unsigned long long* ups, unsigned long long* stamp,
+                                int32_t* queued, int32_t* qgroup, T* rr, T* saved_r, int32_t* list1,
+                                int32_t* glist1, cudaStream_t s) {
+    int m = nfix > nenq ? nfix : nenq;
+    m = m > ngenq ? m : ngenq;
     const int grid = nsrcb + (m + 255) / 256;
-    k_init_sources<T><<<grid, 256, 0, s>>>(nfix, fix_b, fix_p, fix_v, nsrcb, src_bricks, nenq, enq, slot, ups,
-                                           stamp, queued, rr, saved_r, list1);
+    k_init_sources<T><<<grid, 256, 0, s>>>(nfix, fix_b, fix_p, fix_v, nsrcb, src_bricks, nenq, enq, ngenq, genq,
+                                           slot, ups, stamp, queued, qgroup, rr, saved_r, list1, glist1);
     return cudaGetLastError();
 }
 
@@ -931,8 +1071,9 @@ cudaError_t launch_restart_loop(const LoopParams<T>& P, int grid, cudaStream_t s
     template cudaError_t launch_layout_speed<T>(const T*, T*, int, int, int, int, int, int64_t, double, int*,    \
                                                 cudaStream_t);                                                   \
     template cudaError_t launch_init_sources<T>(int, const int32_t*, const int32_t*, const double*, int,         \
-                                                const int32_t*, int, const int32_t*, T*, unsigned long long*,     \
-                                                unsigned long long*, int32_t*, T*, T*, int32_t*, cudaStream_t);    \
+                                                const int32_t*, int, const int32_t*, int, const int32_t*, T*,     \
+                                                unsigned long long*, unsigned long long*, int32_t*, int32_t*, T*,  \
+                                                T*, int32_t*, int32_t*, cudaStream_t);                            \
     template cudaError_t launch_restore_r<T>(int, const int32_t*, const int32_t*, const T*, T*, cudaStream_t);   \
     template cudaError_t launch_gather_r<T>(int, const int32_t*, const int32_t*, const T*, double*,              \
                                             cudaStream_t);                                                       \

@@ -30,8 +30,8 @@ template <typename T>
 cudaError_t launch_layout_speed(const T*, T*, int, int, int, int, int, int64_t, double, int*, cudaStream_t);
 template <typename T>
 cudaError_t launch_init_sources(int, const int32_t*, const int32_t*, const double*, int, const int32_t*, int,
-                                const int32_t*, T*, unsigned long long*, unsigned long long*, int32_t*, T*, T*,
-                                int32_t*, cudaStream_t);
+                                const int32_t*, int, const int32_t*, T*, unsigned long long*, unsigned long long*,
+                                int32_t*, int32_t*, T*, T*, int32_t*, int32_t*, cudaStream_t);
 template <typename T>
 cudaError_t launch_restore_r(int, const int32_t*, const int32_t*, const T*, T*, cudaStream_t);
 template <typename T>
@@ -270,6 +270,7 @@ eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float* F, in
     H.stride = P.stride;
     H.bound = 0.0 + P.stride;
     H.count[1] = nenq;
+    H.mode = 8;
     H.r_rmin_bits = 0x7f800000u;
     H.done = nenq ? 0 : 1;
     // state that must start fresh: stamps and work-list marks (all ones), control block
@@ -282,8 +283,8 @@ eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float* F, in
         NA_CK(cudaMemcpyAsync(d_fv, fv, nfix * sizeof(double), cudaMemcpyHostToDevice, st));
         NA_CK(cudaMemcpyAsync(d_sb, sb, nsb * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         NA_CK(cudaMemcpyAsync(d_enq, enq, nenq * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        NA_CK(eikg::launch_init_sources<float>(nfix, d_fb, d_fp, d_fv, nsb, d_sb, nenq, d_enq, slot, ups, stampv,
-                                               queued, rr, d_saved, list1, st));
+        NA_CK(eikg::launch_init_sources<float>(nfix, d_fb, d_fp, d_fv, nsb, d_sb, nenq, d_enq, 0, nullptr, slot, ups,
+                                               stampv, queued, nullptr, rr, d_saved, list1, nullptr, st));
     }
     if (nenq > 0) {
         int per_sm = 0, sms = 0, dev = 0;
@@ -305,6 +306,8 @@ eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float* F, in
         L.rr = rr;
         L.list0 = list0;
         L.list1 = list1;
+        L.groups = 0;                 // 8^3 blocks only: no group work lists
+        L.mode_fixed = 8;
         L.ctrl = ctrl;
         L.log = nullptr;
         L.log_cap = 0;

@@ -21,8 +21,8 @@ template <typename T>
 cudaError_t launch_layout_speed(const T*, T*, int, int, int, int, int, int64_t, double, int*, cudaStream_t);
 template <typename T>
 cudaError_t launch_init_sources(int, const int32_t*, const int32_t*, const double*, int, const int32_t*, int,
-                                const int32_t*, T*, unsigned long long*, unsigned long long*, int32_t*, T*, T*,
-                                int32_t*, cudaStream_t);
+                                const int32_t*, int, const int32_t*, T*, unsigned long long*, unsigned long long*,
+                                int32_t*, int32_t*, T*, T*, int32_t*, int32_t*, cudaStream_t);
 template <typename T>
 cudaError_t launch_restore_r(int, const int32_t*, const int32_t*, const T*, T*, cudaStream_t);
 template <typename T>
@@ -55,6 +55,11 @@ struct eik_ctx {
     int32_t* queued = nullptr;
     int32_t* list0 = nullptr;
     int32_t* list1 = nullptr;
+    int GX = 0, GY = 0, GZ = 0;
+    int64_t ngroups = 0;
+    int32_t* qgroup = nullptr;
+    int32_t* glist0 = nullptr;
+    int32_t* glist1 = nullptr;
     eikg::Ctrl* ctrl = nullptr;
     int* err_flag = nullptr;
     eikg::RestartRec* log = nullptr;
@@ -102,7 +107,7 @@ cudaError_t dalloc(P** p, size_t bytes) {
 }
 
 void free_all(eik_ctx* c) {
-    void* ptrs[] = {c->rr,    c->slot,  c->ups,   c->stamp,   c->queued, c->list0, c->list1,
+    void* ptrs[] = {c->rr,    c->slot,  c->ups,   c->stamp,   c->queued, c->list0, c->list1, c->qgroup, c->glist0, c->glist1,
                     c->ctrl,  c->err_flag, c->log, c->scratch, c->fstage};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -188,6 +193,10 @@ eik_status eik_create(eik_ctx** out, const int32_t dims[3], double h, const void
     c->BY = (c->ny + 7) / 8;
     c->BZ = (c->nz + 7) / 8;
     c->nbricks = int64_t(c->BX) * c->BY * c->BZ;
+    c->GX = (c->BX + 1) / 2;
+    c->GY = (c->BY + 1) / 2;
+    c->GZ = (c->BZ + 1) / 2;
+    c->ngroups = int64_t(c->GX) * c->GY * c->GZ;
     eik_params_default(&c->params);
 
     auto bail = [&](eik_status s, const std::string& m) {
@@ -214,6 +223,9 @@ eik_status eik_create(eik_ctx** out, const int32_t dims[3], double h, const void
         {reinterpret_cast<void**>(&c->queued), nb * sizeof(int32_t)},
         {reinterpret_cast<void**>(&c->list0), nb * sizeof(int32_t)},
         {reinterpret_cast<void**>(&c->list1), nb * sizeof(int32_t)},
+        {reinterpret_cast<void**>(&c->qgroup), static_cast<size_t>(c->ngroups) * sizeof(int32_t)},
+        {reinterpret_cast<void**>(&c->glist0), static_cast<size_t>(c->ngroups) * sizeof(int32_t)},
+        {reinterpret_cast<void**>(&c->glist1), static_cast<size_t>(c->ngroups) * sizeof(int32_t)},
         {reinterpret_cast<void**>(&c->ctrl), sizeof(eikg::Ctrl)},
         {reinterpret_cast<void**>(&c->err_flag), sizeof(int)},
     };
@@ -386,6 +398,16 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
     }
     std::sort(enq.begin(), enq.end());
     enq.erase(std::unique(enq.begin(), enq.end()), enq.end());
+    const bool groups = (P.block_dim == 16);
+    std::vector<int32_t> genq;
+    if (groups) {
+        for (int32_t b : enq) {
+            const int bx = b % c->BX, by = (b / c->BX) % c->BY, bz = b / (c->BX * c->BY);
+            genq.push_back(((bz >> 1) * c->GY + (by >> 1)) * c->GX + (bx >> 1));
+        }
+        std::sort(genq.begin(), genq.end());
+        genq.erase(std::unique(genq.begin(), genq.end()), genq.end());
+    }
     const int nfix = static_cast<int>(uf.size());
     std::vector<int32_t> fb(nfix), fp(nfix);
     std::vector<double> fv(nfix);
@@ -399,6 +421,7 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
     double* d_fv = reinterpret_cast<double*>(carve(nfix * 8));
     int32_t* d_sb = reinterpret_cast<int32_t*>(carve(sb.size() * 4));
     int32_t* d_enq = reinterpret_cast<int32_t*>(carve(enq.size() * 4));
+    int32_t* d_genq = reinterpret_cast<int32_t*>(carve(genq.size() * 4));
     c->d_saved_r = carve(nfix * sizeof(T));
     c->nfix = nfix;
     if (nfix > 0) {
@@ -407,16 +430,20 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
         EIK_CK(c, cudaMemcpyAsync(d_fv, fv.data(), nfix * 8, cudaMemcpyHostToDevice, s));
         EIK_CK(c, cudaMemcpyAsync(d_sb, sb.data(), sb.size() * 4, cudaMemcpyHostToDevice, s));
         EIK_CK(c, cudaMemcpyAsync(d_enq, enq.data(), enq.size() * 4, cudaMemcpyHostToDevice, s));
+        if (!genq.empty())
+            EIK_CK(c, cudaMemcpyAsync(d_genq, genq.data(), genq.size() * 4, cudaMemcpyHostToDevice, s));
     }
     // ---- Alg. 1 for every brick: untouched (psi = +inf) unless it holds fixed nodes
     const size_t nb = static_cast<size_t>(c->nbricks);
     EIK_CK(c, cudaMemsetAsync(c->stamp, 0xFF, nb * sizeof(unsigned long long), s));
     EIK_CK(c, cudaMemsetAsync(c->queued, 0xFF, nb * sizeof(int32_t), s));
+    if (groups) EIK_CK(c, cudaMemsetAsync(c->qgroup, 0xFF, static_cast<size_t>(c->ngroups) * sizeof(int32_t), s));
     if (nfix > 0)
         EIK_CK(c, eikg::launch_init_sources<T>(nfix, c->d_fix_b, c->d_fix_p, d_fv, static_cast<int>(sb.size()), d_sb,
-                                               static_cast<int>(enq.size()), d_enq, static_cast<T*>(c->slot),
-                                               c->ups, c->stamp, c->queued, static_cast<T*>(c->rr),
-                                               static_cast<T*>(c->d_saved_r), c->list1, s));
+                                               static_cast<int>(enq.size()), d_enq, static_cast<int>(genq.size()),
+                                               d_genq, static_cast<T*>(c->slot), c->ups, c->stamp, c->queued,
+                                               c->qgroup, static_cast<T*>(c->rr), static_cast<T*>(c->d_saved_r),
+                                               c->list1, c->glist1, s));
     // ---- control block: restart 1 with bound_1 = 0 + stride
     eikg::Ctrl& H = c->host_ctrl;
     std::memset(&H, 0, sizeof(H));
@@ -425,6 +452,8 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
     H.stride = P.stride;
     H.bound = 0.0 + P.stride;
     H.count[1] = static_cast<int32_t>(enq.size());
+    H.gcount[1] = static_cast<int32_t>(genq.size());
+    H.mode = groups ? 16 : 8;
     H.r_rmin_bits = 0x7f800000u;
     H.done = enq.empty() ? 1 : 0;
     EIK_CK(c, cudaMemcpyAsync(c->ctrl, &H, sizeof(H), cudaMemcpyHostToDevice, s));
@@ -454,6 +483,14 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
         L.rr = static_cast<const T*>(c->rr);
         L.list0 = c->list0;
         L.list1 = c->list1;
+        L.GX = c->GX;
+        L.GY = c->GY;
+        L.GZ = c->GZ;
+        L.groups = groups ? 1 : 0;
+        L.qgroup = c->qgroup;
+        L.glist0 = c->glist0;
+        L.glist1 = c->glist1;
+        L.mode_fixed = groups ? 16 : 8;
         L.ctrl = c->ctrl;
         L.log = P.log_restarts ? c->log : nullptr;
         L.log_cap = P.log_restarts ? c->log_cap : 0;
@@ -477,7 +514,8 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
 eik_status check_params(eik_ctx* c, const eik_params* p) {
     if (!p) return fail(c, EIK_EINVAL, "params is NULL");
     if (!(p->stride > 0.0)) return fail(c, EIK_EINVAL, "stride must be > 0 (+inf allowed)");
-    if (p->block_dim != 0 && p->block_dim != 8) return fail(c, EIK_ENOTSUP, "block_dim must be 8 (or 0)");
+    if (p->block_dim != 0 && p->block_dim != 8 && p->block_dim != 16)
+        return fail(c, EIK_ENOTSUP, "block_dim must be 8 or 16 (or 0)");
     if (p->schedule != EIK_SCHED_FIXED) return fail(c, EIK_ENOTSUP, "only the fixed-stride schedule is available");
     if (!(p->window >= 0.0) || !std::isfinite(p->window)) return fail(c, EIK_EINVAL, "window must be finite and >= 0");
     if (!(p->fallback_tau >= 0.0) || !(p->fallback_tau <= 1.0))

@@ -94,9 +94,10 @@ def test_random_ragged_grids_fp64(eik, orc, trial):
         F[synth.uniform(trial, 22, F.size).reshape(F.shape) < 0.1] = 0.0
     src = synth.random_sources(trial, 23, dims, h, 1 + trial % 3)
     ref = orc.fmm(F, h, src)
-    for s in (0.5, 2.0, 8.0, math.inf):
-        psi, _ = run(eik, F, h, src, "fp64", s * h)
-        assert_parity(psi, ref, "fp64")
+    for bd in (8, 16):
+        for s in (0.5, 2.0, 8.0, math.inf):
+            psi, _ = run(eik, F, h, src, "fp64", s * h, block_dim=bd)
+            assert_parity(psi, ref, "fp64")
 
 
 @pytest.mark.parametrize("cfg,n", [("C2", 72), ("C3", 64), ("C4", 80)])
@@ -105,10 +106,11 @@ def test_families_fp32(eik, orc, cfg, n):
     w = synth.workload(cfg, n)
     F = w.speed()
     ref = orc.fmm(F, w.h, w.sources)
-    for s in (1.0, 2.0, 4.0, 8.0):
-        psi, st = run(eik, F, w.h, w.sources, "fp32", s * w.h)
-        assert_parity(psi, ref, "fp32")
-        assert st["fallbacks"] == 0
+    for bd in (8, 16):
+        for s in (1.0, 2.0, 4.0, 8.0):
+            psi, st = run(eik, F, w.h, w.sources, "fp32", s * w.h, block_dim=bd)
+            assert_parity(psi, ref, "fp32")
+            assert st["fallbacks"] == 0
 
 
 @pytest.mark.parametrize("cfg,n", [("C2", 56), ("C4", 48)])
@@ -154,8 +156,9 @@ def test_edge_shapes(eik, orc, dims, src):
     for prec in ("fp64", "fp32"):
         Fp = synth.round_to(F, prec)
         refp = orc.fmm(Fp, h, src)
-        psi, _ = run(eik, Fp, h, src, prec, 2 * h)
-        assert_parity(psi, refp, prec)
+        for bd in (8, 16):
+            psi, _ = run(eik, Fp, h, src, prec, 2 * h, block_dim=bd)
+            assert_parity(psi, refp, prec)
 
 
 def test_barrier_wall_and_sealed_region(eik, orc):
@@ -173,8 +176,22 @@ def test_barrier_wall_and_sealed_region(eik, orc):
     ref = orc.fmm(F, h, src)
     assert np.isinf(ref[20, 20, 10]) and np.isinf(ref[0, 0, 30])
     for prec in ("fp64", "fp32"):
-        psi, _ = run(eik, F, h, src, prec, 2 * h)
-        assert_parity(psi, ref, prec)
+        for bd in (8, 16):
+            psi, _ = run(eik, F, h, src, prec, 2 * h, block_dim=bd)
+            assert_parity(psi, ref, prec)
+
+
+def test_group_blocks_cut_refreshes(eik, orc):
+    """16^3 blocks (2x2x2 bricks marched by one CTA) see more of the front per restart: fewer
+    acceptances and solves per node than 8^3 blocks (the paper's Sec. 3.5 block-size effect)."""
+    w = synth.workload("C4", 96)
+    F = w.speed()
+    ref = orc.fmm(F, w.h, w.sources)
+    p8, s8 = run(eik, F, w.h, w.sources, "fp32", 2 * w.h, block_dim=8)
+    p16, s16 = run(eik, F, w.h, w.sources, "fp32", 2 * w.h, block_dim=16)
+    assert_parity(p8, ref, "fp32")
+    assert_parity(p16, ref, "fp32")
+    assert s16["accepted"] < s8["accepted"] and s16["solves"] < s8["solves"]
 
 
 def test_stride_does_not_change_the_solution(eik):
@@ -182,8 +199,8 @@ def test_stride_does_not_change_the_solution(eik):
     w = synth.workload("C3", 64)
     F = w.speed()
     base, _ = run(eik, F, w.h, w.sources, "fp32", 2 * w.h)
-    for s in (0.5, 1.0, 4.0, 16.0, math.inf):
-        psi, _ = run(eik, F, w.h, w.sources, "fp32", s * w.h)
+    for s, bd in ((0.5, 8), (1.0, 8), (4.0, 8), (16.0, 8), (math.inf, 8), (2.0, 16), (8.0, 16)):
+        psi, _ = run(eik, F, w.h, w.sources, "fp32", s * w.h, block_dim=bd)
         fin = np.isfinite(base)
         assert np.array_equal(np.isfinite(psi), fin)
         assert np.max(np.abs(psi[fin] - base[fin])) <= 4 * np.spacing(np.float32(base[fin].max()))
