@@ -92,8 +92,11 @@ eik_status eik_clear_sources(eik_ctx *ctx);
 
 /* Schedules of the restart bound (Alg. 6: bound <- min(bound + stride, width)). */
 typedef enum {
-    EIK_SCHED_FIXED = 0,   /* every restart advances the bound by `stride` */
-    EIK_SCHED_LEARNED = 1  /* a trained network picks the stride per restart (eik_sched_load) */
+    EIK_SCHED_FIXED = 0,   /* every restart advances the bound by `stride` with block edge `block_dim` */
+    EIK_SCHED_LEARNED = 1, /* after each restart the schedule network (eik_set_schedule) picks the stride
+                              and block edge of the next one; `stride` and `block_dim` set restart 1 */
+    EIK_SCHED_RANDOM = 2   /* each restart's stride and block edge drawn from the action table with
+                              `seed` (to record training data) */
 } eik_schedule;
 
 typedef struct {
@@ -107,7 +110,7 @@ typedef struct {
     double fallback_tau;    /* FP32 mode: fall back to double when D < tau * k * (h/F)^2 (0 = default 1/8) */
     int64_t max_restarts;   /* restart cap (0 = default 1 << 24); reaching it returns EIK_ETIMEOUT */
     int32_t log_restarts;   /* non-zero: record per-restart statistics (eik_restart_log) */
-    int32_t reserved;
+    int32_t seed;           /* EIK_SCHED_RANDOM seed */
     void *loop_events[2];   /* optional cudaEvent_t pair the library records on its stream right
                                before and right after the restart-loop kernel (NULL: none) */
 } eik_params;
@@ -130,14 +133,18 @@ typedef struct {
 /* One record per restart when eik_params.log_restarts is set. */
 typedef struct {
     int32_t k;              /* restart index, 1-based */
-    int32_t active;         /* blocks marched in this restart */
+    int32_t active;         /* 8^3 bricks marched in this restart */
     int64_t band;           /* band points left (pending) at the end of the restart */
     int64_t accepted;       /* points accepted in this restart */
+    int64_t solves;         /* upwind solves in this restart */
     double bound;           /* bound_band of this restart */
     double stride;          /* stride that produced this bound */
     double rmin;            /* min h/F over the marched blocks */
     double rmax;            /* max h/F over the marched blocks */
     double ms;              /* device time of the restart */
+    int32_t block_dim;      /* block edge of this restart */
+    int32_t next_action;    /* action chosen for the next restart (-1: fixed schedule) */
+    float features[10];     /* the schedule network's input after this restart */
 } eik_restart_rec;
 
 /* eik_params_default -- fill *p with the defaults above and stride = 2h-equivalent 0 (caller sets stride). */
@@ -183,6 +190,47 @@ const char *eik_last_error(const eik_ctx *ctx);
 
 /* eik_version -- library version string. */
 const char *eik_version(void);
+
+/*
+ * Restart-schedule network (no counterpart in the paper; the paper fixes the
+ * stride).  A multilayer perceptron EIK_SCHED_INPUTS -> EIK_SCHED_HIDDEN (tanh)
+ * -> EIK_SCHED_HIDDEN (tanh) -> EIK_SCHED_ACTIONS maps the front statistics of
+ * restart k (eik_restart_rec.features) to a predicted log cost rate (device
+ * milliseconds per unit of bound advance) for each action of the table
+ * eik_sched_actions; the learned schedule takes the lowest.  Parameters are
+ * EIK_SCHED_PARAMS floats: W1 (hidden x inputs, row-major), b1, W2, b2, W3, b3.
+ * Changing the schedule changes which restart does which work, not psi.
+ */
+#define EIK_SCHED_INPUTS 10
+#define EIK_SCHED_HIDDEN 32
+#define EIK_SCHED_ACTIONS 12
+#define EIK_SCHED_PARAMS (EIK_SCHED_HIDDEN * EIK_SCHED_INPUTS + EIK_SCHED_HIDDEN + \
+                          EIK_SCHED_HIDDEN * EIK_SCHED_HIDDEN + EIK_SCHED_HIDDEN + \
+                          EIK_SCHED_ACTIONS * EIK_SCHED_HIDDEN + EIK_SCHED_ACTIONS)
+
+/* eik_sched_actions -- the action table: stride in units of h and block edge of each action (host). */
+eik_status eik_sched_actions(double *stride_h, int32_t *block_dim, int32_t cap, int32_t *n);
+
+/* eik_set_schedule -- load network weights (host, n = EIK_SCHED_PARAMS finite floats) into the
+ * context for EIK_SCHED_LEARNED; w = NULL unloads them. */
+eik_status eik_set_schedule(eik_ctx *ctx, const float *w, int32_t n);
+
+/* eik_mlp_forward -- Y[B][ACTIONS] = network(X[B][INPUTS]); all DEVICE pointers; async on stream. */
+eik_status eik_mlp_forward(const float *w, const float *X, int32_t B, float *Y, void *stream);
+
+/* eik_mlp_grad -- loss = mean_s (Y[s][act[s]] - tgt[s])^2 and its gradient grad[PARAMS] with respect
+ * to w; DEVICE pointers; work holds eik_mlp_work_floats(B) floats owned by the caller.  The sum over
+ * samples runs in a fixed order, so the result is deterministic. */
+eik_status eik_mlp_grad(const float *w, const float *X, const int32_t *act, const float *tgt, int32_t B,
+                        float *grad, float *loss, float *work, void *stream);
+int32_t eik_mlp_work_floats(int32_t B);
+
+/* eik_mlp_adam -- one Adam step (Kingma and Ba, 2015) on n parameters, step number t >= 1; DEVICE. */
+eik_status eik_mlp_adam(float *w, const float *grad, float *m, float *v, int32_t n, float lr, float b1,
+                        float b2, float eps, int32_t t, void *stream);
+
+/* eik_mlp_last_error -- message of the calling thread's last failed eik_mlp_* call. */
+const char *eik_mlp_last_error(void);
 
 /*
  * eik_solve_noalloc -- one complete solve that allocates no device memory.

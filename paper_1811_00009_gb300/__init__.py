@@ -27,7 +27,10 @@ LIB_PATH = os.path.join(_HERE, "libeik.so")
 
 EIK_OK, EIK_EINVAL, EIK_ENOMEM, EIK_ECUDA, EIK_ETIMEOUT, EIK_ESTATE, EIK_ENOTSUP = range(7)
 EIK_FP32, EIK_FP64 = 0, 1
-EIK_SCHED_FIXED, EIK_SCHED_LEARNED = 0, 1
+EIK_SCHED_FIXED, EIK_SCHED_LEARNED, EIK_SCHED_RANDOM = 0, 1, 2
+SCHED_INPUTS, SCHED_HIDDEN, SCHED_ACTIONS = 10, 32, 12
+SCHED_PARAMS = SCHED_HIDDEN * SCHED_INPUTS + SCHED_HIDDEN + SCHED_HIDDEN * SCHED_HIDDEN + SCHED_HIDDEN + \
+    SCHED_ACTIONS * SCHED_HIDDEN + SCHED_ACTIONS
 STATUS_NAMES = {0: "EIK_OK", 1: "EIK_EINVAL", 2: "EIK_ENOMEM", 3: "EIK_ECUDA", 4: "EIK_ETIMEOUT",
                 5: "EIK_ESTATE", 6: "EIK_ENOTSUP"}
 
@@ -41,7 +44,7 @@ class EikError(RuntimeError):
 class eik_params(C.Structure):
     _fields_ = [("stride", C.c_double), ("block_dim", C.c_int32), ("schedule", C.c_int32),
                 ("window", C.c_double), ("fallback_tau", C.c_double), ("max_restarts", C.c_int64),
-                ("log_restarts", C.c_int32), ("reserved", C.c_int32), ("loop_events", C.c_void_p * 2)]
+                ("log_restarts", C.c_int32), ("seed", C.c_int32), ("loop_events", C.c_void_p * 2)]
 
 
 class eik_stats(C.Structure):
@@ -53,8 +56,9 @@ class eik_stats(C.Structure):
 
 class eik_restart_rec(C.Structure):
     _fields_ = [("k", C.c_int32), ("active", C.c_int32), ("band", C.c_int64), ("accepted", C.c_int64),
-                ("bound", C.c_double), ("stride", C.c_double), ("rmin", C.c_double), ("rmax", C.c_double),
-                ("ms", C.c_double)]
+                ("solves", C.c_int64), ("bound", C.c_double), ("stride", C.c_double), ("rmin", C.c_double),
+                ("rmax", C.c_double), ("ms", C.c_double), ("block_dim", C.c_int32), ("next_action", C.c_int32),
+                ("features", C.c_float * SCHED_INPUTS)]
 
 
 _lock = threading.Lock()
@@ -99,6 +103,21 @@ def lib():
             L.eik_last_error.argtypes = [vp]
             L.eik_version.restype = C.c_char_p
             L.eik_version.argtypes = []
+            fp = C.c_void_p
+            L.eik_set_schedule.restype = i32
+            L.eik_set_schedule.argtypes = [vp, C.POINTER(C.c_float), i32]
+            L.eik_sched_actions.restype = i32
+            L.eik_sched_actions.argtypes = [C.POINTER(dbl), C.POINTER(i32), i32, C.POINTER(i32)]
+            L.eik_mlp_forward.restype = i32
+            L.eik_mlp_forward.argtypes = [fp, fp, i32, fp, vp]
+            L.eik_mlp_grad.restype = i32
+            L.eik_mlp_grad.argtypes = [fp, fp, fp, fp, i32, fp, fp, fp, vp]
+            L.eik_mlp_work_floats.restype = i32
+            L.eik_mlp_work_floats.argtypes = [i32]
+            L.eik_mlp_adam.restype = i32
+            L.eik_mlp_adam.argtypes = [fp, fp, fp, fp, i32, C.c_float, C.c_float, C.c_float, C.c_float, i32, vp]
+            L.eik_mlp_last_error.restype = C.c_char_p
+            L.eik_mlp_last_error.argtypes = []
             _L = L
     return _L
 
@@ -232,7 +251,61 @@ def eik_restart_log(ctx, cap: int = 1 << 16) -> List[Dict[str, Any]]:
     recs = (eik_restart_rec * cap)()
     n = C.c_int64()
     _check(lib().eik_restart_log(ctx, recs, cap, C.byref(n)), ctx)
-    return [{k: getattr(recs[i], k) for k, _ in eik_restart_rec._fields_} for i in range(n.value)]
+    out = []
+    for i in range(n.value):
+        d = {k: getattr(recs[i], k) for k, _ in eik_restart_rec._fields_ if k != "features"}
+        d["features"] = list(recs[i].features)
+        out.append(d)
+    return out
+
+
+# ---- restart-schedule network (no counterpart in the paper) ----
+
+def eik_sched_actions():
+    """[(stride in units of h, block edge)] of every action."""
+    sh = (C.c_double * SCHED_ACTIONS)()
+    bd = (C.c_int32 * SCHED_ACTIONS)()
+    n = C.c_int32()
+    _check(lib().eik_sched_actions(sh, bd, SCHED_ACTIONS, C.byref(n)))
+    return [(sh[i], bd[i]) for i in range(n.value)]
+
+
+def eik_set_schedule(ctx, weights) -> None:
+    """Load the schedule network's weights (host array of SCHED_PARAMS floats) into ctx; None unloads."""
+    if weights is None:
+        _check(lib().eik_set_schedule(ctx, None, 0), ctx)
+        return
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).ravel())
+    _check(lib().eik_set_schedule(ctx, w.ctypes.data_as(C.POINTER(C.c_float)), len(w)), ctx)
+
+
+def _mlp_check(st):
+    if st != EIK_OK:
+        raise EikError(st, lib().eik_mlp_last_error().decode())
+
+
+def _dptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def eik_mlp_forward(w, X, Y, stream=None):
+    """Y[B, ACTIONS] <- network(X[B, INPUTS]); torch CUDA float32 tensors."""
+    _mlp_check(lib().eik_mlp_forward(_dptr(w), _dptr(X), X.shape[0], _dptr(Y), _stream_handle(stream)))
+
+
+def eik_mlp_grad(w, X, act, tgt, grad, loss, work, stream=None):
+    """grad <- d/dw mean (Y[s, act[s]] - tgt[s])^2, loss[0] <- the loss; torch CUDA tensors."""
+    _mlp_check(lib().eik_mlp_grad(_dptr(w), _dptr(X), _dptr(act), _dptr(tgt), X.shape[0], _dptr(grad), _dptr(loss),
+                                  _dptr(work), _stream_handle(stream)))
+
+
+def eik_mlp_work_floats(B: int) -> int:
+    return int(lib().eik_mlp_work_floats(int(B)))
+
+
+def eik_mlp_adam(w, grad, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+    _mlp_check(lib().eik_mlp_adam(_dptr(w), _dptr(grad), _dptr(m), _dptr(v), w.numel(), lr, b1, b2, eps, int(t),
+                                  _stream_handle(stream)))
 
 
 def eik_result(ctx, out):

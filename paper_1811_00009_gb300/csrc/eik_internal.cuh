@@ -82,11 +82,15 @@ struct RestartRec {            // mirrors eik_restart_rec
     int32_t active;
     int64_t band;
     int64_t accepted;
+    int64_t solves;
     double bound;
     double stride;
     double rmin;
     double rmax;
     double ms;
+    int32_t block_dim;
+    int32_t next_action;
+    float features[10];
 };
 
 template <typename T>
@@ -113,10 +117,12 @@ struct LoopParams {
     double fallback_tau;       // FP32: double-precision root when D < tau * k * r^2
     int64_t max_restarts;
     long long wait_limit;      // spin iterations before a barrier wait gives up
-    int32_t sched;             // 0 fixed, 1 learned
+    int32_t sched;             // 0 fixed, 1 learned, 2 seeded random (exploration data)
     int32_t mode_fixed;        // block edge of every restart under the fixed schedule (8 or 16)
     const float* mlp;          // schedule network weights (learned schedule)
     double h;
+    int32_t nmax;              // longest grid axis (feature scale)
+    uint32_t seed;             // random schedule seed
 };
 
 }  // namespace eikg

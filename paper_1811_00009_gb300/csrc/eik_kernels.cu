@@ -21,6 +21,7 @@
 // the start of the next march (see eik_internal.cuh for the double-copy
 // layout that makes this race-free, the argument of Sec. 2.7).
 #include "eik_internal.cuh"
+#include "eik_mlp.cuh"
 
 #include <cfloat>
 #include <cstdint>
@@ -714,13 +715,51 @@ __device__ void march(const LoopParams<T>& P, WarpSmem<T>* SW, int warp, int32_t
     if (lane == 0) acc.band += n;
 }
 
+// Features of the front after restart k for the schedule network (all O(1)):
+// log-counts of marched bricks, band nodes, accepted nodes and solves; log of
+// the largest and smallest speed over the marched bricks; the bound in grid
+// lengths; log k; the stride in h; whether the blocks were 16^3.
+__device__ inline void schedule_features(float* x, double active, double band, double accepted, double solves,
+                                         double rmin, double rmax, double bound, double stride, int k, int mode,
+                                         double h, int nmax) {
+    x[0] = static_cast<float>(log1p(active) / 16.0);
+    x[1] = static_cast<float>(log1p(band) / 20.0);
+    x[2] = static_cast<float>(log1p(accepted) / 20.0);
+    x[3] = (rmin > 0.0 && rmin < 1e300) ? static_cast<float>(log(h / rmin)) : 0.0f;
+    x[4] = (rmax > 0.0 && rmax < 1e300) ? static_cast<float>(log(h / rmax)) : 0.0f;
+    x[5] = static_cast<float>(bound / (h * nmax));
+    x[6] = static_cast<float>(log1p(static_cast<double>(k)) / 8.0);
+    x[7] = static_cast<float>(stride / h / 4.0);
+    x[8] = (mode == 16) ? 1.0f : 0.0f;
+    x[9] = static_cast<float>(log1p(solves) / 20.0);
+    for (int i = 0; i < kIn; ++i) {
+        if (!(x[i] == x[i])) x[i] = 0.0f;
+        x[i] = fminf(10.0f, fmaxf(-10.0f, x[i]));
+    }
+}
+
+__device__ inline unsigned mix32(unsigned a) {
+    a ^= a >> 16;
+    a *= 0x7feb352du;
+    a ^= a >> 15;
+    a *= 0x846ca68bu;
+    a ^= a >> 16;
+    return a;
+}
+
 // Grid barrier at the end of restart k.  The CTA arriving last does the
-// restart bookkeeping of Alg. 6 (statistics, exit test, next bound) before
-// releasing the others.  Returns false when this CTA must leave the loop.
+// restart bookkeeping of Alg. 6 (statistics, exit test, next bound) and, for
+// the learned schedule, evaluates the schedule network with its threads to
+// pick the stride and block edge of restart k+1, before releasing the others.
+// Returns false when this CTA must leave the loop.
 template <typename T>
 __device__ bool end_of_restart(const LoopParams<T>& P) {
     __shared__ int s_last;
     __shared__ int s_ok;
+    __shared__ float s_x[kIn];
+    __shared__ float s_h1[kHid];
+    __shared__ float s_h2[kHid];
+    __shared__ float s_y[kAct];
     Ctrl* C = P.ctrl;
     __syncthreads();
     unsigned gen = 0;
@@ -732,33 +771,90 @@ __device__ bool end_of_restart(const LoopParams<T>& P) {
         s_ok = 1;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        if (s_last) {
+    if (s_last) {
+        if (threadIdx.x == 0) {
             __threadfence();
+            const int k = __ldcg(&C->k);
+            const int mode = __ldcg(&C->mode);
+            const int par = k & 1;
+            const int n_this = (mode == 16) ? __ldcg(&C->gcount[par]) : __ldcg(&C->count[par]);
+            schedule_features(s_x, static_cast<double>(n_this) * (mode == 16 ? 8 : 1),
+                              static_cast<double>(__ldcg(&C->r_band)), static_cast<double>(__ldcg(&C->r_accepted)),
+                              static_cast<double>(__ldcg(&C->r_solves)),
+                              static_cast<double>(__uint_as_float(__ldcg(&C->r_rmin_bits))),
+                              static_cast<double>(__uint_as_float(__ldcg(&C->r_rmax_bits))), __ldcg(&C->bound),
+                              __ldcg(&C->stride), k, mode, P.h, P.nmax);
+        }
+        __syncthreads();
+        if (P.sched == 1 && P.mlp != nullptr) {
+            // the schedule network, one neuron per thread, layer by layer
+            const float* w = P.mlp;
+            const int t = threadIdx.x;
+            if (t < kHid) {
+                float a = w[kOffB1 + t];
+                for (int j = 0; j < kIn; ++j) a += w[kOffW1 + t * kIn + j] * s_x[j];
+                s_h1[t] = tanhf(a);
+            }
+            __syncthreads();
+            if (t < kHid) {
+                float a = w[kOffB2 + t];
+                for (int j = 0; j < kHid; ++j) a += w[kOffW2 + t * kHid + j] * s_h1[j];
+                s_h2[t] = tanhf(a);
+            }
+            __syncthreads();
+            if (t < kAct) {
+                float a = w[kOffB3 + t];
+                for (int j = 0; j < kHid; ++j) a += w[kOffW3 + t * kHid + j] * s_h2[j];
+                s_y[t] = a;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
             const int k = __ldcg(&C->k);
             const int par = k & 1;
             const int mode = __ldcg(&C->mode);
             const int n_this = (mode == 16) ? __ldcg(&C->gcount[par]) : __ldcg(&C->count[par]);
-            const int next_mode = P.mode_fixed;
+            // the next restart's stride and block edge
+            double next_stride = __ldcg(&C->stride);
+            int next_mode = P.mode_fixed;
+            int action = -1;
+            if (P.sched == 1 && P.mlp != nullptr) {
+                action = 0;
+                for (int a = 1; a < kAct; ++a)
+                    if (s_y[a] < s_y[action]) action = a;           // lowest predicted cost rate
+                if (!(s_y[action] == s_y[action])) action = -1;    // network output unusable: keep the fixed stride
+            } else if (P.sched == 2) {
+                action = static_cast<int>(mix32(P.seed * 0x9e3779b9u + static_cast<unsigned>(k)) % kAct);
+            }
+            if (action >= 0) {
+                next_stride = action_stride_h(action) * P.h;
+                next_mode = action_block(action);
+            }
+            if (!P.groups) next_mode = 8;
             const int n_next = (next_mode == 16) ? __ldcg(&C->gcount[par ^ 1]) : __ldcg(&C->count[par ^ 1]);
             const unsigned long long now = globaltimer();
             const unsigned long long acc_a = __ldcg(&C->r_accepted), acc_band = __ldcg(&C->r_band);
+            const unsigned long long acc_s = __ldcg(&C->r_solves);
             if (P.log != nullptr && k - 1 < P.log_cap) {
                 RestartRec rec;
                 rec.k = k;
-                rec.active = n_this;
+                rec.active = n_this * (mode == 16 ? 8 : 1);
                 rec.band = static_cast<int64_t>(acc_band);
                 rec.accepted = static_cast<int64_t>(acc_a);
+                rec.solves = static_cast<int64_t>(acc_s);
                 rec.bound = __ldcg(&C->bound);
                 rec.stride = __ldcg(&C->stride);
                 rec.rmin = __uint_as_float(__ldcg(&C->r_rmin_bits));
                 rec.rmax = __uint_as_float(__ldcg(&C->r_rmax_bits));
                 rec.ms = static_cast<double>(now - __ldcg(&C->t_restart)) * 1e-6;
+                rec.block_dim = mode;
+                rec.next_action = action;
+                for (int i = 0; i < kIn; ++i) rec.features[i] = s_x[i];
                 P.log[k - 1] = rec;
             }
             C->marches += static_cast<unsigned long long>(n_this) * (mode == 16 ? 8ull : 1ull);
             C->accepted += acc_a;
-            C->solves += __ldcg(&C->r_solves);
+            C->solves += acc_s;
             C->updates += __ldcg(&C->r_updates);
             C->fallbacks += __ldcg(&C->r_fallbacks);
             C->rounds += __ldcg(&C->r_rounds);
@@ -782,27 +878,27 @@ __device__ bool end_of_restart(const LoopParams<T>& P) {
                 C->status |= kStRestartCap;
                 C->t_end = now;
             } else {
-                const double s = __ldcg(&C->stride);
                 const double bnd = __ldcg(&C->bound);
                 C->k = k + 1;
                 C->mode = next_mode;
+                C->stride = next_stride;
                 C->bound_prev = bnd;
-                C->bound = bnd + s;                 // bound_band <- bound_band + stride (width = +inf)
+                C->bound = bnd + next_stride;               // bound_band <- bound_band + stride (width = +inf)
                 C->t_restart = now;
             }
             C->bar_count = 0;
             __threadfence();
             st_release(&C->bar_gen, gen + 1);
-        } else {
-            long long it = 0;
-            while (ld_acquire(&C->bar_gen) == gen) {
-                if (++it > P.wait_limit) {
-                    atomicOr(&C->status, kStWaitTimeout);
-                    s_ok = 0;
-                    break;
-                }
-                __nanosleep(64);
+        }
+    } else if (threadIdx.x == 0) {
+        long long it = 0;
+        while (ld_acquire(&C->bar_gen) == gen) {
+            if (++it > P.wait_limit) {
+                atomicOr(&C->status, kStWaitTimeout);
+                s_ok = 0;
+                break;
             }
+            __nanosleep(64);
         }
     }
     __syncthreads();

@@ -318,6 +318,8 @@ eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float* F, in
         L.sched = EIK_SCHED_FIXED;
         L.mlp = nullptr;
         L.h = h;
+        L.nmax = std::max(nx, std::max(ny, nz));
+        L.seed = 0;
         NA_CK(eikg::launch_restart_loop<float>(L, per_sm * sms, st));
     }
     if (nfix > 0) NA_CK(eikg::launch_restore_r<float>(nfix, d_fb, d_fp, d_saved, rr, st));

@@ -7,6 +7,7 @@
 // at the fixed nodes.  Everything runs on the context's stream.
 #include "eik.h"
 #include "eik_internal.cuh"
+#include "eik_mlp.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -62,6 +63,7 @@ struct eik_ctx {
     int32_t* glist1 = nullptr;
     eikg::Ctrl* ctrl = nullptr;
     int* err_flag = nullptr;
+    float* d_mlp = nullptr;        // schedule network weights (eik_set_schedule)
     eikg::RestartRec* log = nullptr;
     int64_t log_cap = 0;
     void* scratch = nullptr;       // per-solve tables of the fixed nodes
@@ -108,7 +110,7 @@ cudaError_t dalloc(P** p, size_t bytes) {
 
 void free_all(eik_ctx* c) {
     void* ptrs[] = {c->rr,    c->slot,  c->ups,   c->stamp,   c->queued, c->list0, c->list1, c->qgroup, c->glist0, c->glist1,
-                    c->ctrl,  c->err_flag, c->log, c->scratch, c->fstage};
+                    c->ctrl,  c->err_flag, c->log, c->scratch, c->fstage, c->d_mlp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -248,6 +250,22 @@ eik_status eik_create(eik_ctx** out, const int32_t dims[3], double h, const void
         return bail(EIK_ECUDA, std::string("eik_create: occupancy query: ") + cudaGetErrorString(e));
     c->loop_grid = per_sm * c->sms;
     *out = c;
+    return EIK_OK;
+}
+
+eik_status eik_set_schedule(eik_ctx* c, const float* w, int32_t n) {
+    if (!c) return fail(nullptr, EIK_EINVAL, "eik_set_schedule: ctx is NULL");
+    if (c->in_flight) return fail(c, EIK_ESTATE, "eik_set_schedule: a solve is in flight");
+    if (!w) {
+        if (c->d_mlp) cudaFree(c->d_mlp);
+        c->d_mlp = nullptr;
+        return EIK_OK;
+    }
+    if (n != eikg::kParams) return fail(c, EIK_EINVAL, "eik_set_schedule: n must be EIK_SCHED_PARAMS");
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(w[i])) return fail(c, EIK_EINVAL, "eik_set_schedule: weights must be finite");
+    if (!c->d_mlp) EIK_CK(c, cudaMalloc(&c->d_mlp, sizeof(float) * eikg::kParams));
+    EIK_CK(c, cudaMemcpy(c->d_mlp, w, sizeof(float) * eikg::kParams, cudaMemcpyHostToDevice));
     return EIK_OK;
 }
 
@@ -398,7 +416,7 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
     }
     std::sort(enq.begin(), enq.end());
     enq.erase(std::unique(enq.begin(), enq.end()), enq.end());
-    const bool groups = (P.block_dim == 16);
+    const bool groups = (P.block_dim == 16) || (P.schedule != EIK_SCHED_FIXED);
     std::vector<int32_t> genq;
     if (groups) {
         for (int32_t b : enq) {
@@ -453,7 +471,7 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
     H.bound = 0.0 + P.stride;
     H.count[1] = static_cast<int32_t>(enq.size());
     H.gcount[1] = static_cast<int32_t>(genq.size());
-    H.mode = groups ? 16 : 8;
+    H.mode = (P.block_dim == 16) ? 16 : 8;
     H.r_rmin_bits = 0x7f800000u;
     H.done = enq.empty() ? 1 : 0;
     EIK_CK(c, cudaMemcpyAsync(c->ctrl, &H, sizeof(H), cudaMemcpyHostToDevice, s));
@@ -490,7 +508,7 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
         L.qgroup = c->qgroup;
         L.glist0 = c->glist0;
         L.glist1 = c->glist1;
-        L.mode_fixed = groups ? 16 : 8;
+        L.mode_fixed = (P.block_dim == 16) ? 16 : 8;
         L.ctrl = c->ctrl;
         L.log = P.log_restarts ? c->log : nullptr;
         L.log_cap = P.log_restarts ? c->log_cap : 0;
@@ -499,8 +517,10 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
         L.max_restarts = P.max_restarts;
         L.wait_limit = (long long)1 << 26;
         L.sched = P.schedule;
-        L.mlp = nullptr;
+        L.mlp = (P.schedule == EIK_SCHED_LEARNED) ? c->d_mlp : nullptr;
         L.h = c->h;
+        L.nmax = std::max(c->nx, std::max(c->ny, c->nz));
+        L.seed = static_cast<uint32_t>(P.seed);
         if (P.loop_events[0]) EIK_CK(c, cudaEventRecord(static_cast<cudaEvent_t>(P.loop_events[0]), s));
         EIK_CK(c, eikg::launch_restart_loop<T>(L, c->loop_grid, s));
         if (P.loop_events[1]) EIK_CK(c, cudaEventRecord(static_cast<cudaEvent_t>(P.loop_events[1]), s));
@@ -516,7 +536,10 @@ eik_status check_params(eik_ctx* c, const eik_params* p) {
     if (!(p->stride > 0.0)) return fail(c, EIK_EINVAL, "stride must be > 0 (+inf allowed)");
     if (p->block_dim != 0 && p->block_dim != 8 && p->block_dim != 16)
         return fail(c, EIK_ENOTSUP, "block_dim must be 8 or 16 (or 0)");
-    if (p->schedule != EIK_SCHED_FIXED) return fail(c, EIK_ENOTSUP, "only the fixed-stride schedule is available");
+    if (p->schedule != EIK_SCHED_FIXED && p->schedule != EIK_SCHED_LEARNED && p->schedule != EIK_SCHED_RANDOM)
+        return fail(c, EIK_EINVAL, "schedule must be EIK_SCHED_FIXED, EIK_SCHED_LEARNED or EIK_SCHED_RANDOM");
+    if (p->schedule == EIK_SCHED_LEARNED && !c->d_mlp)
+        return fail(c, EIK_ESTATE, "learned schedule requested but no weights were loaded (eik_set_schedule)");
     if (!(p->window >= 0.0) || !std::isfinite(p->window)) return fail(c, EIK_EINVAL, "window must be finite and >= 0");
     if (!(p->fallback_tau >= 0.0) || !(p->fallback_tau <= 1.0))
         return fail(c, EIK_EINVAL, "fallback_tau must lie in [0, 1]");

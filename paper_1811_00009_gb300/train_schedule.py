@@ -1,0 +1,198 @@
+"""Train the restart-schedule network from the solver's own per-restart timings.
+
+Data: solves of seeded synthetic grids of the three speed families (seeds
+distinct from the evaluation workloads), each run with every fixed action of
+the table (stride x block edge) and with the seeded random schedule, recording
+per-restart logs (features after restart k, device time of each restart).
+Sample for restart k: input = features after k, action = the one used for
+restart k+1, target = log of the cost rate of the next `horizon` restarts
+(device ms per unit h of bound advance).  Training runs on the GPU with the
+library's own kernels (eik_mlp_grad / eik_mlp_adam), full batch, Adam.
+
+    python -m paper_1811_00009_gb300.train_schedule --out weights.json [--eval]
+
+--eval then times the 512^3 layered workload (16 z-layers, source at
+(0.5, 0.5, 0.1)) with every fixed action and with the learned schedule.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+DEFAULT_WEIGHTS = os.path.join(HERE, "schedule_weights.json")
+
+
+def load_weights(path: str = DEFAULT_WEIGHTS):
+    with open(path) as fh:
+        d = json.load(fh)
+    return np.asarray(d["weights"], dtype=np.float32), d
+
+
+def _solve(eik, ctx, stride, **kw):
+    st = eik.eik_solve_ex(ctx, stride, log_restarts=1, **kw)
+    return st, eik.eik_restart_log(ctx)
+
+
+def collect(eik, grids, actions, random_runs=3, log=print):
+    """Per-restart records of fixed-action and random-schedule runs on each grid."""
+    import torch
+    import synth
+    runs = []
+    for (fam, n, seed) in grids:
+        w = synth.workload({"sines": "C2", "layers": "C3", "grf": "C4"}[fam], n)
+        w.seed = seed
+        w.sources = synth.random_sources(seed, 40, w.dims, w.h, 1 + seed % 2)
+        F = w.speed_torch(torch.device("cuda")).float().contiguous()
+        ctx = eik.eik_create(w.dims, w.h, F, "fp32")
+        eik.eik_add_sources(ctx, w.sources)
+        eik.eik_solve_ex(ctx, 2 * w.h)                        # warm-up
+        for a, (sh, bd) in enumerate(actions):
+            st, recs = _solve(eik, ctx, sh * w.h, block_dim=bd)
+            runs.append({"grid": (fam, n, seed), "h": w.h, "fixed": a, "recs": recs, "ms": st["device_ms"]})
+        for r in range(random_runs):
+            st, recs = _solve(eik, ctx, 2 * w.h, schedule=eik.EIK_SCHED_RANDOM, seed=1000 * seed + r)
+            runs.append({"grid": (fam, n, seed), "h": w.h, "fixed": -1, "recs": recs, "ms": st["device_ms"]})
+        eik.eik_destroy(ctx)
+        log(f"collected {fam} {n}^3 seed {seed}: {len(runs)} runs")
+    return runs
+
+
+def dataset(runs, horizon=2):
+    X, A, Y = [], [], []
+    for run in runs:
+        recs, h = run["recs"], run["h"]
+        for i in range(len(recs) - 1):
+            a = run["fixed"] if run["fixed"] >= 0 else recs[i]["next_action"]
+            nxt = recs[i + 1:i + 1 + horizon]
+            ms = sum(r["ms"] for r in nxt)
+            adv = sum(r["stride"] for r in nxt) / h
+            if ms <= 0 or not (adv > 0) or not math.isfinite(adv):
+                continue
+            X.append(recs[i]["features"])
+            A.append(a)
+            Y.append(math.log(ms / adv))
+    return np.asarray(X, np.float32), np.asarray(A, np.int32), np.asarray(Y, np.float32)
+
+
+def train(eik, X, A, Y, steps=3000, lr=3e-3, seed=1811, log=print):
+    import torch
+    import synth
+    n = eik.SCHED_PARAMS
+    rng = synth.normal(seed, 1, n)
+    # layer-wise scaled initial weights, zero biases
+    w = np.zeros(n, np.float32)
+    o = 0
+    for rows, cols in ((32, 10), (32, 0), (32, 32), (32, 0), (12, 32), (12, 0)):
+        cnt = rows * max(cols, 1) if cols else rows
+        if cols:
+            w[o:o + cnt] = rng[o:o + cnt] / math.sqrt(cols)
+        o += cnt
+    w[o - 12:o] = float(np.mean(Y))                           # output biases start at the mean target
+    perm = np.argsort(synth.uniform(seed, 2, len(Y)))
+    nval = max(1, len(Y) // 10)
+    val, tr = perm[:nval], perm[nval:]
+    dev = torch.device("cuda")
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    wd = T(w)
+    Xt, At, Yt = T(X[tr]), T(A[tr]), T(Y[tr])
+    Xv, Av, Yv = T(X[val]), T(A[val]), T(Y[val])
+    g = torch.zeros(n, dtype=torch.float32, device=dev)
+    m = torch.zeros_like(g)
+    v = torch.zeros_like(g)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    work = torch.zeros(eik.eik_mlp_work_floats(max(len(tr), nval)), dtype=torch.float32, device=dev)
+    hist = []
+    for t in range(1, steps + 1):
+        eik.eik_mlp_grad(wd, Xt, At, Yt, g, loss, work)
+        eik.eik_mlp_adam(wd, g, m, v, t, lr=lr if t < steps // 2 else lr / 3)
+        if t % 500 == 0 or t == 1:
+            tl = loss.item()
+            eik.eik_mlp_grad(wd, Xv, Av, Yv, g, loss, work)
+            hist.append((t, tl, loss.item()))
+            log(f"step {t}: train {tl:.4f} val {loss.item():.4f}")
+    return wd.cpu().numpy(), hist
+
+
+def evaluate(eik, weights, n=512, reps=3, log=print):
+    """Device time of the layered workload under every fixed action and under the learned schedule."""
+    import torch
+    import synth
+    w = synth.workload("C3", n)
+    F = w.speed_torch(torch.device("cuda")).float().contiguous()
+    ctx = eik.eik_create(w.dims, w.h, F, "fp32")
+    eik.eik_add_sources(ctx, w.sources)
+    eik.eik_set_schedule(ctx, weights)
+    res = {}
+    def t(**kw):
+        eik.eik_solve_ex(ctx, **kw)
+        best = math.inf
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = eik.eik_solve_ex(ctx, **kw)
+            best = min(best, time.perf_counter() - t0)
+        return best * 1e3, st
+    for a, (sh, bd) in enumerate(eik.eik_sched_actions()):
+        ms, st = t(stride=sh * w.h, block_dim=bd)
+        res[f"fixed_{sh:g}h_b{bd}"] = ms
+        log(f"fixed {sh:g}h b{bd}: {ms:.2f} ms, {st['restarts']} restarts")
+    ms, st = t(stride=2 * w.h, block_dim=8, schedule=eik.EIK_SCHED_LEARNED)
+    res["learned"] = ms
+    log(f"learned: {ms:.2f} ms, {st['restarts']} restarts")
+    eik.eik_destroy(ctx)
+    best_fixed = min(v for k, v in res.items() if k.startswith("fixed"))
+    res["best_fixed"] = best_fixed
+    res["learned_over_best_fixed"] = res["learned"] / best_fixed
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=DEFAULT_WEIGHTS)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--eval", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="small data set (tests)")
+    args = ap.parse_args()
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1811_00009_gb300 as eik
+    torch.cuda.set_device(0)
+    actions = eik.eik_sched_actions()
+    if args.quick:
+        grids = [("grf", 96, 21), ("layers", 96, 22)]
+    else:
+        grids = [(fam, n, 100 + 10 * i + j) for i, fam in enumerate(("sines", "layers", "grf"))
+                 for j, n in enumerate((160, 256, 352))]
+    t0 = time.time()
+    runs = collect(eik, grids, actions)
+    X, A, Y = dataset(runs)
+    print(f"dataset: {len(Y)} samples from {len(runs)} runs in {time.time() - t0:.1f} s", flush=True)
+    w, hist = train(eik, X, A, Y, steps=args.steps)
+    meta = {"weights": [float(v) for v in w], "samples": int(len(Y)), "runs": len(runs),
+            "grids": grids, "history": hist, "actions": actions,
+            "features": ["log1p(active bricks)/16", "log1p(band)/20", "log1p(accepted)/20", "log F_max",
+                         "log F_min", "bound/(h*nmax)", "log1p(k)/8", "stride/h/4", "16^3 blocks",
+                         "log1p(solves)/20"],
+            "target": "log(device ms per h of bound advance over the next 2 restarts)"}
+    if args.eval:
+        meta["eval_512_layers"] = evaluate(eik, w)
+        print(json.dumps(meta["eval_512_layers"]), flush=True)
+    with open(args.out, "w") as fh:
+        json.dump(meta, fh)
+    print("wrote", args.out)
+
+
+if __name__ == "__main__":
+    main()
