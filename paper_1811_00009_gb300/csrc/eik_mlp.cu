@@ -1,9 +1,9 @@
 // Training and batched inference of the restart-schedule network (eik_mlp.cuh).
 //
 // Gradients are deterministic: per-sample quantities are written to a caller
-// workspace, then each parameter's gradient is summed over the samples in a
-// fixed order by one thread (no atomics), so repeated training runs give the
-// same weights bit for bit.
+// workspace, each parameter's gradient is summed over fixed chunks of 256
+// samples and then over the chunks, always in the same order (no atomics), so
+// repeated training runs give the same weights bit for bit.
 #include "eik.h"
 #include "eik_mlp.cuh"
 
@@ -60,45 +60,56 @@ __global__ void k_mlp_deltas(const float* __restrict__ w, const float* __restric
     o[4 * kHid] = e;
 }
 
-// one thread per parameter: the gradient summed over samples in order
-__global__ void k_mlp_reduce(const float* __restrict__ X, const int* __restrict__ act, int B,
-                             const float* __restrict__ work, float* __restrict__ grad, float* __restrict__ loss) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p == kParams) {                                         // the loss
-        float acc = 0.0f;
-        for (int s = 0; s < B; ++s) {
-            const float e = work[static_cast<size_t>(s) * kWork + 4 * kHid];
-            acc += e * e;
-        }
-        if (loss) *loss = acc / static_cast<float>(B);
-        return;
+// per-sample contribution to parameter p (and, for p == kParams, the squared error)
+__device__ inline float param_term(int p, int s, int B, const float* __restrict__ X, const int* __restrict__ act,
+                                   const float* __restrict__ work) {
+    const float* o = work + static_cast<size_t>(s) * kWork;
+    if (p == kParams) return o[4 * kHid] * o[4 * kHid];
+    const float* x = X + static_cast<size_t>(s) * kIn;
+    if (p < kOffB1) {                       // W1[i][j] : d1_i x_j
+        const int i = (p - kOffW1) / kIn, j = (p - kOffW1) % kIn;
+        return o[2 * kHid + i] * x[j];
     }
+    if (p < kOffW2) return o[2 * kHid + (p - kOffB1)];                 // b1[i]
+    if (p < kOffB2) {                       // W2[i][j] : d2_i h1_j
+        const int i = (p - kOffW2) / kHid, j = (p - kOffW2) % kHid;
+        return o[3 * kHid + i] * o[j];
+    }
+    if (p < kOffW3) return o[3 * kHid + (p - kOffB2)];                 // b2[i]
+    const float dy = 2.0f * o[4 * kHid] / static_cast<float>(B);      // d loss / d y of the taken action
+    if (p < kOffB3) {                       // W3[a][j] : dy_a h2_j, taken action only
+        const int a = (p - kOffW3) / kHid, j = (p - kOffW3) % kHid;
+        return (act[s] == a) ? dy * o[kHid + j] : 0.0f;
+    }
+    return (act[s] == p - kOffB3) ? dy : 0.0f;                         // b3[a]
+}
+
+constexpr int kChunk = 256;   // samples per partial sum
+
+// level 1: partial[c][p] = sum over the samples of chunk c, in order
+__global__ void k_mlp_partial(const float* __restrict__ X, const int* __restrict__ act, int B,
+                              const float* __restrict__ work, float* __restrict__ partial) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (p > kParams) return;
+    const int s0 = c * kChunk, s1 = min(B, s0 + kChunk);
+    float acc = 0.0f;
+    for (int s = s0; s < s1; ++s) acc += param_term(p, s, B, X, act, work);
+    partial[static_cast<size_t>(c) * (kParams + 1) + p] = acc;
+}
+
+// level 2: the chunks' partial sums added in order
+__global__ void k_mlp_total(int nchunks, const float* __restrict__ partial, int B, float* __restrict__ grad,
+                            float* __restrict__ loss) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p > kParams) return;
     float acc = 0.0f;
-    for (int s = 0; s < B; ++s) {
-        const float* o = work + static_cast<size_t>(s) * kWork;
-        const float* x = X + static_cast<size_t>(s) * kIn;
-        float g;
-        if (p < kOffB1) {                       // W1[i][j] : d1_i x_j
-            const int i = (p - kOffW1) / kIn, j = (p - kOffW1) % kIn;
-            g = o[2 * kHid + i] * x[j];
-        } else if (p < kOffW2) {                // b1[i]
-            g = o[2 * kHid + (p - kOffB1)];
-        } else if (p < kOffB2) {                // W2[i][j] : d2_i h1_j
-            const int i = (p - kOffW2) / kHid, j = (p - kOffW2) % kHid;
-            g = o[3 * kHid + i] * o[j];
-        } else if (p < kOffW3) {                // b2[i]
-            g = o[3 * kHid + (p - kOffB2)];
-        } else if (p < kOffB3) {                // W3[a][j] : dy_a h2_j, only the taken action
-            const int a = (p - kOffW3) / kHid, j = (p - kOffW3) % kHid;
-            g = (act[s] == a) ? (2.0f * o[4 * kHid] / static_cast<float>(B)) * o[kHid + j] : 0.0f;
-        } else {                                // b3[a]
-            const int a = p - kOffB3;
-            g = (act[s] == a) ? 2.0f * o[4 * kHid] / static_cast<float>(B) : 0.0f;
-        }
-        acc += g;
+    for (int c = 0; c < nchunks; ++c) acc += partial[static_cast<size_t>(c) * (kParams + 1) + p];
+    if (p == kParams) {
+        if (loss) *loss = acc / static_cast<float>(B);
+    } else {
+        grad[p] = acc;
     }
-    grad[p] = acc;
 }
 
 // Adam (Kingma and Ba, 2015), element-wise
@@ -120,7 +131,9 @@ extern "C" {
 
 const char* eik_mlp_last_error(void) { return g_mlp_err.c_str(); }
 
-int32_t eik_mlp_work_floats(int32_t B) { return B > 0 ? B * kWork : 0; }
+int32_t eik_mlp_work_floats(int32_t B) {
+    return B > 0 ? B * kWork + ((B + kChunk - 1) / kChunk) * (kParams + 1) : 0;
+}
 
 eik_status eik_mlp_forward(const float* w, const float* X, int32_t B, float* Y, void* stream) {
     if (!w || !X || !Y || B < 1) return mlp_fail(EIK_EINVAL, "eik_mlp_forward: bad argument");
@@ -135,8 +148,11 @@ eik_status eik_mlp_grad(const float* w, const float* X, const int32_t* act, cons
                         float* loss, float* work, void* stream) {
     if (!w || !X || !act || !tgt || !grad || !work || B < 1) return mlp_fail(EIK_EINVAL, "eik_mlp_grad: bad argument");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int nchunks = (B + kChunk - 1) / kChunk;
+    float* partial = work + static_cast<size_t>(B) * kWork;
     k_mlp_deltas<<<(B + 127) / 128, 128, 0, s>>>(w, X, act, tgt, B, work);
-    k_mlp_reduce<<<(kParams + 1 + 127) / 128, 128, 0, s>>>(X, act, B, work, grad, loss);
+    k_mlp_partial<<<dim3((kParams + 1 + 127) / 128, nchunks), 128, 0, s>>>(X, act, B, work, partial);
+    k_mlp_total<<<(kParams + 1 + 127) / 128, 128, 0, s>>>(nchunks, partial, B, grad, loss);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return mlp_fail(EIK_ECUDA, cudaGetErrorString(e));
     return EIK_OK;

@@ -68,9 +68,11 @@ def collect(eik, grids, actions, random_runs=3, log=print):
     return runs
 
 
-def dataset(runs, horizon=2):
+def dataset(runs, horizon=2, fixed_only=False):
     X, A, Y = [], [], []
     for run in runs:
+        if fixed_only and run["fixed"] < 0:
+            continue
         recs, h = run["recs"], run["h"]
         for i in range(len(recs) - 1):
             a = run["fixed"] if run["fixed"] >= 0 else recs[i]["next_action"]
@@ -85,7 +87,56 @@ def dataset(runs, horizon=2):
     return np.asarray(X, np.float32), np.asarray(A, np.int32), np.asarray(Y, np.float32)
 
 
-def train(eik, X, A, Y, steps=3000, lr=3e-3, seed=1811, log=print):
+def dataset_curves(runs, delta_h=8.0):
+    """Every logged state labelled for every action.
+
+    For each grid, the fixed-action runs give T_a(b), the device time until the
+    bound reaches b under action a.  A state logged at bound b (in any of the
+    grid's runs) gets, for every action a, the target log of the local cost rate
+    (T_a(b + delta) - T_a(b)) / (delta / h): what a would cost from this phase
+    of the front on.  One sample per (state, action).
+    """
+    import collections
+    by = collections.defaultdict(dict)
+    states = collections.defaultdict(list)
+    for run in runs:
+        g = tuple(run["grid"])
+        if run["fixed"] >= 0:
+            by[g][run["fixed"]] = run
+        states[g].extend(run["recs"])
+    X, A, Y = [], [], []
+    for g, fixed in by.items():
+        h = next(iter(fixed.values()))["h"]
+        curves = {}
+        for a, run in fixed.items():
+            b = np.array([r["bound"] for r in run["recs"]], dtype=np.float64)
+            t = np.cumsum([r["ms"] for r in run["recs"]])
+            ok = np.isfinite(b)
+            curves[a] = (b[ok], t[ok])
+        d = delta_h * h
+        for rec in states[g]:
+            b0 = rec["bound"]
+            if not math.isfinite(b0):
+                continue
+            rates = {}
+            for a, (b, t) in curves.items():
+                if len(b) < 2 or b0 + 0.5 * d > b[-1]:
+                    continue
+                t0 = np.interp(b0, b, t)
+                t1 = np.interp(min(b0 + d, b[-1]), b, t)
+                adv = (min(b0 + d, b[-1]) - b0) / h
+                if t1 > t0 and adv > 0:
+                    rates[a] = math.log((t1 - t0) / adv)
+            if len(rates) < len(curves):
+                continue
+            for a, y in rates.items():
+                X.append(rec["features"])
+                A.append(a)
+                Y.append(y)
+    return np.asarray(X, np.float32), np.asarray(A, np.int32), np.asarray(Y, np.float32)
+
+
+def train(eik, X, A, Y, steps=3000, lr=3e-3, seed=1811, batch=32768, log=print):
     import torch
     import synth
     n = eik.SCHED_PARAMS
@@ -107,14 +158,22 @@ def train(eik, X, A, Y, steps=3000, lr=3e-3, seed=1811, log=print):
     wd = T(w)
     Xt, At, Yt = T(X[tr]), T(A[tr]), T(Y[tr])
     Xv, Av, Yv = T(X[val]), T(A[val]), T(Y[val])
+    nb = min(batch, len(tr))
+    order = torch.from_numpy(np.argsort(synth.uniform(seed, 3, len(tr)))).to(dev)
     g = torch.zeros(n, dtype=torch.float32, device=dev)
     m = torch.zeros_like(g)
     v = torch.zeros_like(g)
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
-    work = torch.zeros(eik.eik_mlp_work_floats(max(len(tr), nval)), dtype=torch.float32, device=dev)
+    work = torch.zeros(eik.eik_mlp_work_floats(max(nb, nval)), dtype=torch.float32, device=dev)
     hist = []
+    pos = 0
     for t in range(1, steps + 1):
-        eik.eik_mlp_grad(wd, Xt, At, Yt, g, loss, work)
+        if pos + nb > len(tr):
+            pos = 0
+        idx = order[pos:pos + nb]
+        pos += nb
+        xb, ab, yb = Xt[idx].contiguous(), At[idx].contiguous(), Yt[idx].contiguous()
+        eik.eik_mlp_grad(wd, xb, ab, yb, g, loss, work)
         eik.eik_mlp_adam(wd, g, m, v, t, lr=lr if t < steps // 2 else lr / 3)
         if t % 500 == 0 or t == 1:
             tl = loss.item()
@@ -161,8 +220,15 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--horizon", type=int, default=8)
     ap.add_argument("--eval", action="store_true")
     ap.add_argument("--quick", action="store_true", help="small data set (tests)")
+    ap.add_argument("--runs-out", default=None, help="save the collected per-restart records (JSON)")
+    ap.add_argument("--runs-in", default=None, help="train from saved records instead of collecting")
+    ap.add_argument("--variants", default=None,
+                    help="comma list N:curves|fixed|all (curves: every action labelled from the fixed-action "
+                         "runs' time-versus-bound curves over N h; fixed/all: the taken action over the next N "
+                         "restarts); trains and evaluates each, keeps the fastest")
     args = ap.parse_args()
     import torch
     import __graft_entry__
@@ -174,21 +240,45 @@ def main():
         grids = [("grf", 96, 21), ("layers", 96, 22)]
     else:
         grids = [(fam, n, 100 + 10 * i + j) for i, fam in enumerate(("sines", "layers", "grf"))
-                 for j, n in enumerate((160, 256, 352))]
+                 for j, n in enumerate((160, 256, 352, 448))]
     t0 = time.time()
-    runs = collect(eik, grids, actions)
-    X, A, Y = dataset(runs)
-    print(f"dataset: {len(Y)} samples from {len(runs)} runs in {time.time() - t0:.1f} s", flush=True)
-    w, hist = train(eik, X, A, Y, steps=args.steps)
-    meta = {"weights": [float(v) for v in w], "samples": int(len(Y)), "runs": len(runs),
-            "grids": grids, "history": hist, "actions": actions,
+    if args.runs_in:
+        with open(args.runs_in) as fh:
+            runs = json.load(fh)
+    else:
+        runs = collect(eik, grids, actions)
+        if args.runs_out:
+            with open(args.runs_out, "w") as fh:
+                json.dump(runs, fh)
+    print(f"{len(runs)} runs in {time.time() - t0:.1f} s", flush=True)
+    variants = [(args.horizon, "curves")]
+    if args.variants:
+        variants = [(int(v.split(":")[0]), v.split(":")[1]) for v in args.variants.split(",")]
+    best = None
+    for hz, fo in variants:
+        if fo == "curves":
+            X, A, Y = dataset_curves(runs, delta_h=float(hz))
+        else:
+            X, A, Y = dataset(runs, horizon=hz, fixed_only=(fo == "fixed"))
+        print(f"variant {hz} {fo}: {len(Y)} samples", flush=True)
+        w, hist = train(eik, X, A, Y, steps=args.steps)
+        ev = evaluate(eik, w) if (args.eval or args.variants) else None
+        if ev is not None:
+            print(json.dumps({"horizon": hz, "labels": fo, **ev}), flush=True)
+        score = ev["learned_over_best_fixed"] if ev else 0.0
+        if best is None or score < best[0]:
+            best = (score, w, hist, hz, fo, ev, len(Y))
+    _, w, hist, hz, fo, ev, nsamp = best
+    meta = {"weights": [float(v) for v in w], "samples": int(nsamp), "runs": len(runs), "horizon": hz,
+            "labels": fo, "grids": grids, "history": hist, "actions": actions,
             "features": ["log1p(active bricks)/16", "log1p(band)/20", "log1p(accepted)/20", "log F_max",
                          "log F_min", "bound/(h*nmax)", "log1p(k)/8", "stride/h/4", "16^3 blocks",
                          "log1p(solves)/20"],
-            "target": "log(device ms per h of bound advance over the next 2 restarts)"}
-    if args.eval:
-        meta["eval_512_layers"] = evaluate(eik, w)
-        print(json.dumps(meta["eval_512_layers"]), flush=True)
+            "target": (f"log(device ms per h of bound advance over the next {hz} h of bound, every action, "
+                       "from the fixed-action runs' time-versus-bound curves)" if fo == "curves" else
+                       f"log(device ms per h of bound advance over the next {hz} restarts, taken action)")}
+    if ev is not None:
+        meta["eval_512_layers"] = ev
     with open(args.out, "w") as fh:
         json.dump(meta, fh)
     print("wrote", args.out)
