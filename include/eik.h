@@ -113,6 +113,8 @@ typedef struct {
     int32_t seed;           /* EIK_SCHED_RANDOM seed */
     void *loop_events[2];   /* optional cudaEvent_t pair the library records on its stream right
                                before and right after the restart-loop kernel (NULL: none) */
+    double switch_margin;   /* EIK_SCHED_LEARNED: keep the current action unless another one's predicted
+                               log cost rate is lower by more than this (default 0.02) */
 } eik_params;
 
 /* Per-solve statistics, filled by eik_solve / eik_wait. */

@@ -63,7 +63,7 @@ struct Ctrl {
     int32_t gcount[2];         // group (16^3 block) work-list lengths, by restart parity
     int32_t ghead[2];          // next group work-list entry to hand out
     int32_t mode;              // block edge of restart k: 8 (one warp per brick) or 16 (one CTA per group)
-    int32_t pad0;
+    int32_t action;            // schedule action of restart k (-1: none yet)
     double bound;              // bound_band of restart k
     double bound_prev;         // bound_band of restart k-1 (-1 at k = 1)
     double stride;             // stride that produced `bound`
@@ -123,6 +123,7 @@ struct LoopParams {
     double h;
     int32_t nmax;              // longest grid axis (feature scale)
     uint32_t seed;             // random schedule seed
+    float margin;              // learned schedule: switch action only if predicted cheaper by this much (log)
 };
 
 }  // namespace eikg

@@ -822,6 +822,8 @@ __device__ bool end_of_restart(const LoopParams<T>& P) {
                 action = 0;
                 for (int a = 1; a < kAct; ++a)
                     if (s_y[a] < s_y[action]) action = a;           // lowest predicted cost rate
+                const int cur = __ldcg(&C->action);
+                if (cur >= 0 && s_y[cur] - s_y[action] <= P.margin) action = cur;   // not worth a switch
                 if (!(s_y[action] == s_y[action])) action = -1;    // network output unusable: keep the fixed stride
             } else if (P.sched == 2) {
                 action = static_cast<int>(mix32(P.seed * 0x9e3779b9u + static_cast<unsigned>(k)) % kAct);
@@ -881,6 +883,7 @@ __device__ bool end_of_restart(const LoopParams<T>& P) {
                 const double bnd = __ldcg(&C->bound);
                 C->k = k + 1;
                 C->mode = next_mode;
+                C->action = action;
                 C->stride = next_stride;
                 C->bound_prev = bnd;
                 C->bound = bnd + next_stride;               // bound_band <- bound_band + stride (width = +inf)

@@ -21,12 +21,13 @@ constexpr int kOffB2 = kOffW2 + kHid * kHid;
 constexpr int kOffW3 = kOffB2 + kHid;
 constexpr int kOffB3 = kOffW3 + kAct * kHid;
 
-// Actions: stride (in units of h) x block edge.
+// Actions: (stride in units of h, block edge).  Eight strides with 8^3 blocks
+// and four with 16^3 blocks.
 __host__ __device__ inline double action_stride_h(int a) {
-    const double s[6] = {0.5, 1.0, 1.5, 2.0, 3.0, 4.0};
-    return s[a % 6];
+    const double s[kAct] = {1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0, 5.0, 2.0, 3.0, 4.0, 6.0};
+    return s[a];
 }
-__host__ __device__ inline int action_block(int a) { return a < 6 ? 8 : 16; }
+__host__ __device__ inline int action_block(int a) { return a < 8 ? 8 : 16; }
 
 // One sample, one thread: outputs y and (optionally) the hidden activations.
 __device__ inline void mlp_forward_one(const float* __restrict__ w, const float* x, float* y, float* h1o, float* h2o) {

@@ -271,6 +271,7 @@ eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float* F, in
     H.bound = 0.0 + P.stride;
     H.count[1] = nenq;
     H.mode = 8;
+    H.action = -1;
     H.r_rmin_bits = 0x7f800000u;
     H.done = nenq ? 0 : 1;
     // state that must start fresh: stamps and work-list marks (all ones), control block

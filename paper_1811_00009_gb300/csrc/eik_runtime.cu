@@ -166,6 +166,7 @@ void eik_params_default(eik_params* p) {
     p->fallback_tau = 0.125;
     p->max_restarts = int64_t(1) << 24;
     p->log_restarts = 0;
+    p->switch_margin = 0.02;
 }
 
 eik_status eik_create(eik_ctx** out, const int32_t dims[3], double h, const void* F, int F_on_device,
@@ -466,6 +467,7 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
     eikg::Ctrl& H = c->host_ctrl;
     std::memset(&H, 0, sizeof(H));
     H.k = enq.empty() ? 0 : 1;
+    H.action = -1;
     H.bound_prev = -1.0;
     H.stride = P.stride;
     H.bound = 0.0 + P.stride;
@@ -521,6 +523,7 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
         L.h = c->h;
         L.nmax = std::max(c->nx, std::max(c->ny, c->nz));
         L.seed = static_cast<uint32_t>(P.seed);
+        L.margin = static_cast<float>(P.switch_margin);
         if (P.loop_events[0]) EIK_CK(c, cudaEventRecord(static_cast<cudaEvent_t>(P.loop_events[0]), s));
         EIK_CK(c, eikg::launch_restart_loop<T>(L, c->loop_grid, s));
         if (P.loop_events[1]) EIK_CK(c, cudaEventRecord(static_cast<cudaEvent_t>(P.loop_events[1]), s));

@@ -144,12 +144,13 @@ def train(eik, X, A, Y, steps=3000, lr=3e-3, seed=1811, batch=32768, log=print):
     # layer-wise scaled initial weights, zero biases
     w = np.zeros(n, np.float32)
     o = 0
-    for rows, cols in ((32, 10), (32, 0), (32, 32), (32, 0), (12, 32), (12, 0)):
+    for rows, cols in ((eik.SCHED_HIDDEN, eik.SCHED_INPUTS), (eik.SCHED_HIDDEN, 0), (eik.SCHED_HIDDEN, eik.SCHED_HIDDEN),
+                       (eik.SCHED_HIDDEN, 0), (eik.SCHED_ACTIONS, eik.SCHED_HIDDEN), (eik.SCHED_ACTIONS, 0)):
         cnt = rows * max(cols, 1) if cols else rows
         if cols:
             w[o:o + cnt] = rng[o:o + cnt] / math.sqrt(cols)
         o += cnt
-    w[o - 12:o] = float(np.mean(Y))                           # output biases start at the mean target
+    w[o - eik.SCHED_ACTIONS:o] = float(np.mean(Y))            # output biases start at the mean target
     perm = np.argsort(synth.uniform(seed, 2, len(Y)))
     nval = max(1, len(Y) // 10)
     val, tr = perm[:nval], perm[nval:]
@@ -206,9 +207,11 @@ def evaluate(eik, weights, n=512, reps=3, log=print):
         ms, st = t(stride=sh * w.h, block_dim=bd)
         res[f"fixed_{sh:g}h_b{bd}"] = ms
         log(f"fixed {sh:g}h b{bd}: {ms:.2f} ms, {st['restarts']} restarts")
-    ms, st = t(stride=2 * w.h, block_dim=8, schedule=eik.EIK_SCHED_LEARNED)
-    res["learned"] = ms
-    log(f"learned: {ms:.2f} ms, {st['restarts']} restarts")
+    for mg in (0.0, 0.02, 0.05):
+        ms, st = t(stride=2 * w.h, block_dim=8, schedule=eik.EIK_SCHED_LEARNED, switch_margin=mg)
+        res[f"learned_margin_{mg:g}"] = ms
+        log(f"learned (margin {mg:g}): {ms:.2f} ms, {st['restarts']} restarts")
+    res["learned"] = res["learned_margin_0.02"]
     eik.eik_destroy(ctx)
     best_fixed = min(v for k, v in res.items() if k.startswith("fixed"))
     res["best_fixed"] = best_fixed
@@ -240,7 +243,7 @@ def main():
         grids = [("grf", 96, 21), ("layers", 96, 22)]
     else:
         grids = [(fam, n, 100 + 10 * i + j) for i, fam in enumerate(("sines", "layers", "grf"))
-                 for j, n in enumerate((160, 256, 352, 448))]
+                 for j, n in enumerate((160, 256, 352, 448, 512))]
     t0 = time.time()
     if args.runs_in:
         with open(args.runs_in) as fh:

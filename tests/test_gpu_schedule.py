@@ -95,13 +95,14 @@ def test_learned_schedule_needs_weights(eik):
 
 
 def test_learned_schedule_decides_from_the_network(eik, orc):
-    """With a given network the schedule takes, after every restart, the action of lowest output."""
+    """With a given network (and no switching margin) the schedule takes, after every restart, the
+    action of lowest output."""
     from oracle import mlp
     w = synth.workload("C3", 80)
     F = synth.round_to(w.speed(), "fp32")
     ref = orc.fmm(F, w.h, w.sources)
     weights = (synth.normal(77, 1, mlp.n_params()) * 0.5).astype(np.float32)
-    psi, st, log = solve(eik, w, F, schedule=eik.EIK_SCHED_LEARNED, weights=weights)
+    psi, st, log = solve(eik, w, F, schedule=eik.EIK_SCHED_LEARNED, weights=weights, switch_margin=0.0)
     for r in log[:-1]:
         y, _, _ = mlp.forward(weights.astype(np.float64), np.array([r["features"]], dtype=np.float64))
         assert y[0][r["next_action"]] <= y[0].min() + 1e-4     # the lowest output, up to FP32 rounding
