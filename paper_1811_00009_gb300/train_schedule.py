@@ -136,6 +136,46 @@ def dataset_curves(runs, delta_h=8.0):
     return np.asarray(X, np.float32), np.asarray(A, np.int32), np.asarray(Y, np.float32)
 
 
+def dataset_rollout(runs):
+    """Every logged state labelled for every action with the time to finish.
+
+    For each grid, the fixed-action runs give T_a(b) (device time until the
+    bound reaches b under action a) and T_a(end).  A state logged at bound b in
+    any of the grid's runs gets, for every action a, the target
+    log(T_a(end) - T_a(b) + 0.01 ms): the measured cost of finishing the solve
+    from this phase of the front with a.  Taking the lowest at every restart is
+    one step of policy improvement over the fixed-stride schedules (a rollout
+    policy), so it can only beat the best of them to the extent that these
+    values hold for the states it visits.
+    """
+    import collections
+    by = collections.defaultdict(dict)
+    states = collections.defaultdict(list)
+    for run in runs:
+        g = tuple(run["grid"])
+        if run["fixed"] >= 0:
+            by[g][run["fixed"]] = run
+        states[g].extend(run["recs"])
+    X, A, Y = [], [], []
+    for g, fixed in by.items():
+        curves = {}
+        for a, run in fixed.items():
+            b = np.array([r["bound"] for r in run["recs"]], dtype=np.float64)
+            t = np.cumsum([r["ms"] for r in run["recs"]])
+            ok = np.isfinite(b)
+            curves[a] = (b[ok], t[ok], t[-1])
+        for rec in states[g]:
+            b0 = rec["bound"]
+            if not math.isfinite(b0):
+                continue
+            for a, (b, t, tend) in curves.items():
+                rem = tend - (np.interp(b0, b, t) if len(b) else 0.0)
+                X.append(rec["features"])
+                A.append(a)
+                Y.append(math.log(max(rem, 0.0) + 0.01))
+    return np.asarray(X, np.float32), np.asarray(A, np.int32), np.asarray(Y, np.float32)
+
+
 def train(eik, X, A, Y, steps=3000, lr=3e-3, seed=1811, batch=32768, log=print):
     import torch
     import synth
@@ -229,9 +269,10 @@ def main():
     ap.add_argument("--runs-out", default=None, help="save the collected per-restart records (JSON)")
     ap.add_argument("--runs-in", default=None, help="train from saved records instead of collecting")
     ap.add_argument("--variants", default=None,
-                    help="comma list N:curves|fixed|all (curves: every action labelled from the fixed-action "
-                         "runs' time-versus-bound curves over N h; fixed/all: the taken action over the next N "
-                         "restarts); trains and evaluates each, keeps the fastest")
+                    help="comma list N:rollout|curves|fixed|all (rollout: every action labelled with the time "
+                         "its fixed-action run needed to finish from the state's bound; curves: the local cost "
+                         "rate over N h; fixed/all: the taken action over the next N restarts); trains and "
+                         "evaluates each, keeps the fastest")
     args = ap.parse_args()
     import torch
     import __graft_entry__
@@ -254,13 +295,15 @@ def main():
             with open(args.runs_out, "w") as fh:
                 json.dump(runs, fh)
     print(f"{len(runs)} runs in {time.time() - t0:.1f} s", flush=True)
-    variants = [(args.horizon, "curves")]
+    variants = [(0, "rollout")]
     if args.variants:
         variants = [(int(v.split(":")[0]), v.split(":")[1]) for v in args.variants.split(",")]
     best = None
     for hz, fo in variants:
         if fo == "curves":
             X, A, Y = dataset_curves(runs, delta_h=float(hz))
+        elif fo == "rollout":
+            X, A, Y = dataset_rollout(runs)
         else:
             X, A, Y = dataset(runs, horizon=hz, fixed_only=(fo == "fixed"))
         print(f"variant {hz} {fo}: {len(Y)} samples", flush=True)
@@ -277,9 +320,10 @@ def main():
             "features": ["log1p(active bricks)/16", "log1p(band)/20", "log1p(accepted)/20", "log F_max",
                          "log F_min", "bound/(h*nmax)", "log1p(k)/8", "stride/h/4", "16^3 blocks",
                          "log1p(solves)/20"],
-            "target": (f"log(device ms per h of bound advance over the next {hz} h of bound, every action, "
-                       "from the fixed-action runs' time-versus-bound curves)" if fo == "curves" else
-                       f"log(device ms per h of bound advance over the next {hz} restarts, taken action)")}
+            "target": {"rollout": "log(device ms to finish the solve from the state's bound with the action, from "
+                                  "the fixed-action runs) + 0.01 ms",
+                       "curves": f"log(device ms per h of bound advance over the next {hz} h, every action)"}.get(
+                           fo, f"log(device ms per h of bound advance over the next {hz} restarts, taken action)")}
     if ev is not None:
         meta["eval_512_layers"] = ev
     with open(args.out, "w") as fh:
