@@ -193,6 +193,11 @@ def run_ours(args):
     eik.eik_add_sources(ctx, w.sources)
     stride = args.stride_h * w.h
     kw = {"window": args.window} if args.window else {}
+    if args.schedule == "learned":
+        from paper_1811_00009_gb300.train_schedule import load_weights
+        weights, _ = load_weights()
+        eik.eik_set_schedule(ctx, weights)
+        kw["schedule"] = eik.EIK_SCHED_LEARNED
 
     for _ in range(args.warmup):
         st = eik.eik_solve_ex(ctx, stride, **kw)
@@ -225,6 +230,16 @@ def run_ours(args):
         elapsed_ms = float(t.item())
     total_points = w.npoints * args.steps * ws
     value = total_points / (elapsed_ms * 1e-3) / 1e6
+
+    # the same workload with the fixed stride (the method without the schedule network)
+    sched_cmp = None
+    if args.schedule == "learned":
+        kf = {k: v for k, v in kw.items() if k != "schedule"}
+        fx = [eik.eik_solve_ex(ctx, stride, **kf)["device_ms"] for _ in range(2)]
+        ln = [s_["device_ms"] for s_ in stats]
+        sched_cmp = {"learned_device_ms": min(ln), "fixed_device_ms": min(fx),
+                     "fixed_stride_h": args.stride_h, "learned_over_fixed": min(ln) / min(fx),
+                     "learned_restarts": stats[-1]["restarts"]}
 
     # roofline of the dominant kernel (the restart loop), algorithmic bytes per launch
     peak, peak_kind = measured_peaks()
@@ -267,6 +282,8 @@ def run_ours(args):
         Fs = torch.from_numpy(F_s.astype(np.float32 if prec == "fp32" else np.float64)).to(dev)
         c2 = eik.eik_create(w_s.dims, w_s.h, Fs, prec)
         eik.eik_add_sources(c2, w_s.sources)
+        if args.schedule == "learned":
+            eik.eik_set_schedule(c2, weights)
         eik.eik_solve_ex(c2, args.stride_h * w_s.h, **kw)
         o = torch.empty_like(Fs)
         eik.eik_result(c2, o)
@@ -284,12 +301,13 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
             "data": "synthetic",
             "config": {"workload": (f"C4: {n}^3 node grid, h=1/{n - 1}, F=exp(g) random field std 0.5 corr 0.05, "
-                                    f"centre source, {prec.upper()} (FP64 root fallback), fixed stride "
-                                    f"{args.stride_h:g}h, 8^3 blocks"),
-                       "grid": [n, n, n], "stride_h": args.stride_h, "block": 8, "schedule": "fixed",
+                                    f"centre source, {prec.upper()} (FP64 root fallback), "
+                                    + ("learned stride/block schedule" if args.schedule == "learned" else
+                                       f"fixed stride {args.stride_h:g}h, 8^3 blocks")),
+                       "grid": [n, n, n], "stride_h": args.stride_h, "block": 8, "schedule": args.schedule,
                        "l2": "inputs larger than L2 (F and psi copies are GiB-sized), no flush",
                        "parallelism": "independent solve per GPU" if ws > 1 else "single GPU"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "schedule": sched_cmp,
             "gpu_launches": KERNELS_PER_SOLVE * args.steps, "clocks": clocks,
             "solve": {"restarts": s0["restarts"], "marches": s0["marches"], "accepted": s0["accepted"],
                       "solves": s0["solves"], "updates": s0["updates"], "fallbacks": s0["fallbacks"],
@@ -310,7 +328,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=1024, help="grid edge of the workload (default 1024)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
-    ap.add_argument("--stride-h", type=float, default=2.0)
+    ap.add_argument("--stride-h", type=float, default=2.0, help="fixed stride, and restart 1 of the learned schedule")
+    ap.add_argument("--schedule", choices=["learned", "fixed"], default="learned")
     ap.add_argument("--window", type=float, default=0.0)
     ap.add_argument("--cpu-n", type=int, default=160)
     ap.add_argument("--ref-n", type=int, default=128)

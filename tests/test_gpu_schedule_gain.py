@@ -1,0 +1,72 @@
+"""What the trained schedule network gains over the method without it.
+
+The method without the network advances the bound by one fixed stride per
+restart; the paper recommends about 2h (Sec. 3.5-3.6), which is also the best
+single fixed setting of the action table across the three workload families
+here.  With the committed weights (trained by train_schedule.py on the GPU from
+the solver's own timings, on grids whose seeds differ from these), the learned
+schedule must reach the same solution and spend no more device time in total
+over one workload of each family than the fixed 2h stride; the measured ratio
+is printed.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eik():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1811_00009_gb300 import build
+    build.build()
+    import paper_1811_00009_gb300 as E
+    return E
+
+
+def best_of(eik, ctx, reps=3, **kw):
+    eik.eik_solve_ex(ctx, **kw)
+    best = None
+    for _ in range(reps):
+        st = eik.eik_solve_ex(ctx, **kw)
+        if best is None or st["device_ms"] < best["device_ms"]:
+            best = st
+    return best
+
+
+def test_learned_schedule_versus_fixed_stride(eik):
+    import torch
+    from paper_1811_00009_gb300.train_schedule import load_weights
+    weights, meta = load_weights()
+    tot_fixed = tot_learned = 0.0
+    for cfg in ("C2", "C3", "C4"):
+        w = synth.workload(cfg, 384)
+        F = w.speed_torch(torch.device("cuda")).float().contiguous()
+        ctx = eik.eik_create(w.dims, w.h, F, "fp32")
+        try:
+            eik.eik_add_sources(ctx, w.sources)
+            eik.eik_set_schedule(ctx, weights)
+            sf = best_of(eik, ctx, stride=2 * w.h, block_dim=8)
+            a = torch.empty_like(F)
+            eik.eik_result(ctx, a)
+            sl = best_of(eik, ctx, stride=2 * w.h, block_dim=8, schedule=eik.EIK_SCHED_LEARNED)
+            b = torch.empty_like(F)
+            eik.eik_result(ctx, b)
+            torch.cuda.synchronize()
+        finally:
+            eik.eik_destroy(ctx)
+        a, b = a.cpu().numpy(), b.cpu().numpy()
+        fin = np.isfinite(a)
+        assert np.array_equal(fin, np.isfinite(b))
+        assert np.max(np.abs(a[fin] - b[fin])) <= 4 * np.spacing(np.float32(a[fin].max()))
+        assert sl["restarts"] != sf["restarts"]                 # the schedule adapts the stride
+        tot_fixed += sf["device_ms"]
+        tot_learned += sl["device_ms"]
+        print(f"{cfg} 384^3: fixed 2h {sf['device_ms']:.2f} ms ({sf['restarts']} restarts), "
+              f"learned {sl['device_ms']:.2f} ms ({sl['restarts']} restarts)")
+    print(f"total: fixed 2h {tot_fixed:.2f} ms, learned {tot_learned:.2f} ms, ratio {tot_learned / tot_fixed:.3f}")
+    assert tot_learned <= 1.01 * tot_fixed
