@@ -33,6 +33,10 @@ if ROOT not in sys.path:
 METRIC = "Eikonal Mpoints/s at 512^3/1024^3 + HBM roofline %; learned vs fixed stride"
 ALGO_BYTES_PER_POINT = {"fp32": 8, "fp64": 16}      # read F once + write psi once
 KERNELS_PER_SOLVE = 4                                # gather_r, init_sources, restart_loop, restore_r
+# DRAM bytes per node of one k_restart_loop launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum
+# = 394.05 MB for the C4 family at 256^3, fixed stride 2h, 8^3 blocks, FP32; profiles/k_restart_loop_c4_256_fixed2h.md),
+# scaled to a full launch by the node count.
+NCU_TRAFFIC_PER_NODE = {"fp32": 394.05e6 / 256 ** 3}
 
 
 def measured_peaks():
@@ -246,8 +250,11 @@ def run_ours(args):
     algo_bytes = ALGO_BYTES_PER_POINT[prec] * w.npoints
     loop_avg_ms = sum(loop_ms) / len(loop_ms)
     achieved = algo_bytes / (loop_avg_ms * 1e-3) / 1e9
+    traffic = NCU_TRAFFIC_PER_NODE.get(prec)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "k_restart_loop", "peak_kind": peak_kind,
+            "traffic": traffic * w.npoints if traffic else None,
+            "traffic_source": "ncu capture at 256^3 (fixed 2h) scaled by the node count" if traffic else None,
+            "kernel": "k_restart_loop", "peak_kind": peak_kind,
             "algo_bytes_per_launch": algo_bytes, "launch_ms": loop_avg_ms}
 
     # end to end through the public API with host buffers (pinned), per step:
