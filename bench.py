@@ -33,10 +33,10 @@ if ROOT not in sys.path:
 METRIC = "Eikonal Mpoints/s at 512^3/1024^3 + HBM roofline %; learned vs fixed stride"
 ALGO_BYTES_PER_POINT = {"fp32": 8, "fp64": 16}      # read F once + write psi once
 KERNELS_PER_SOLVE = 4                                # gather_r, init_sources, restart_loop, restore_r
-# DRAM bytes per node of one k_restart_loop launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum
-# = 394.05 MB for the C4 family at 256^3, fixed stride 2h, 8^3 blocks, FP32; profiles/k_restart_loop_c4_256_fixed2h.md),
-# scaled to a full launch by the node count.
-NCU_TRAFFIC_PER_NODE = {"fp32": 394.05e6 / 256 ** 3}
+# DRAM bytes per node of one k_restart_loop launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum for
+# the C4 family at 256^3, fixed stride 2h, 8^3 blocks, FP32), scaled to a full launch by the node count; empty
+# until the current kernel has been captured.
+NCU_TRAFFIC_PER_NODE = {}
 
 
 def measured_peaks():
@@ -127,6 +127,24 @@ def cpu_oracle_sample(n: int, seed_cfg: str = "C4"):
     return w, F, psi, dt
 
 
+def cpu_block_sample(n: int):
+    """Time the CPU form of the paper's method (Alg. 6, OpenMP over blocks, FP64) on all host cores,
+    block edge 32 and stride 2h (the paper's parallel optimum), on the workload family at n^3."""
+    import oracle
+    import synth
+    w = synth.workload("C4", n)
+    F = w.speed()
+    oracle.build()
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    _, st = oracle.block_fmm(F, w.h, w.sources, 32, 2.0 * w.h, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": w.npoints / dt / 1e6, "unit": "Mpoints/s", "cores": cores,
+            "kind": "oracle block solver (Alg. 6 with OpenMP)",
+            "sample": f"one full solve of the C4 family at {n}^3, block 32, stride 2h, FP64, {dt:.2f} s, "
+                      f"{st['nr']} restarts"}
+
+
 def run_reference(args):
     ws, rank, _ = setup_dist()
     if rank != 0:
@@ -159,6 +177,56 @@ def run_reference(args):
     return 0
 
 
+def batch_bench(eik, synth, steps: int, warmup: int, tune_rounds: int, dev):
+    """The batched launch: 64 grids (edges 32..192 per axis, 1-4 sources, sines /
+    layers / GRF speeds, FP32) solved together; solves/s and per-solve latency
+    percentiles with the autotuned tiles, and with the untuned default tiles
+    (8^3 blocks, stride 2h) beside them."""
+    import numpy as np
+    import torch
+    ws = synth.batch_workloads(64)
+    grids = [(w.dims, w.h, w.speed_torch(dev), w.sources) for w in ws]
+    stream = torch.cuda.current_stream()
+    B = eik.Batch(grids, "fp32", stream=stream)
+    try:
+        t0 = time.perf_counter()
+        tiles, ctas, tune_ms = B.autotune(rounds=tune_rounds)
+        tune_s = time.perf_counter() - t0
+
+        def timed(tl, ctas_per_sm):
+            for _ in range(warmup):
+                B.solve(tl, ctas_per_sm=ctas_per_sm)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            lat, ms, restarts = [], [], 0
+            for a, b in ev:
+                a.record(stream)
+                B.solve_async(tl, ctas_per_sm=ctas_per_sm)
+                b.record(stream)
+                st = B.wait()
+                restarts = st["restarts"]
+                lat += [r["done_ms"] for r in B.info()]
+            torch.cuda.synchronize()
+            ms = [a.elapsed_time(b) for a, b in ev]
+            lat = np.array(lat)
+            return {"solves_per_s": 64 * steps / (sum(ms) * 1e-3), "ms_per_batch": sum(ms) / steps,
+                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                    "mpoints_per_s": sum(w.npoints for w in ws) * steps / (sum(ms) * 1e-3) / 1e6,
+                    "restarts": restarts}
+
+        tuned = timed(None, 0)
+        default = timed([(8, 2.0 * w.h) for w in ws], 0)
+        info = B.info()
+    finally:
+        B.close()
+    e8 = sum(1 for t in tiles if t[0] == 8)
+    f = sorted({round(t[1] / (t[0] * r["rmin"]), 4) for t, r in zip(tiles, info)})
+    return {"grids": 64, "points": int(sum(w.npoints for w in ws)), "autotuned": tuned,
+            "default_8_2h": default, "tuned_over_default_ms": tuned["ms_per_batch"] / default["ms_per_batch"],
+            "tiles": {"ctas_per_sm": ctas, "blocks_8": e8, "blocks_16": 64 - e8, "stride_factor": f,
+                      "tune_seconds": tune_s, "tune_best_ms": tune_ms},
+            "latency": "per grid: device time from the start of the launch to the end of its last restart"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -179,6 +247,8 @@ def run_ours(args):
         cpu = {"value": w_s.npoints / dt / 1e6, "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
                "sample": f"one full solve of the C4 family at {args.cpu_n}^3 (same F recipe, h=1/{args.cpu_n - 1}, "
                          f"centre source) by the single-heap FP64 fast marching oracle, one thread, {dt:.1f} s"}
+        if args.cpu_block_n:
+            cpu["block_solver"] = cpu_block_sample(args.cpu_block_n)
 
     import __graft_entry__
     __graft_entry__.build()
@@ -301,6 +371,9 @@ def run_ours(args):
                "grid": [args.cpu_n] * 3, "tolerance": 1e-5 if prec == "fp32" else None}
 
     eik.eik_destroy(ctx)
+    batch = None
+    if not args.no_batch and rank == 0:
+        batch = batch_bench(eik, synth, args.batch_steps, 3, args.tune_rounds, dev)
     clocks = clk.summary()
     s0 = stats[-1]
     line = {"metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": ws, "steps": args.steps,
@@ -319,7 +392,7 @@ def run_ours(args):
             "solve": {"restarts": s0["restarts"], "marches": s0["marches"], "accepted": s0["accepted"],
                       "solves": s0["solves"], "updates": s0["updates"], "fallbacks": s0["fallbacks"],
                       "rounds": s0["rounds"], "loop_ms": loop_avg_ms},
-            "error_vs_oracle": err}
+            "error_vs_oracle": err, "batch": batch}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -339,10 +412,14 @@ def main():
     ap.add_argument("--schedule", choices=["learned", "fixed"], default="learned")
     ap.add_argument("--window", type=float, default=0.0)
     ap.add_argument("--cpu-n", type=int, default=160)
+    ap.add_argument("--cpu-block-n", type=int, default=256, help="grid edge of the multi-core CPU block-solver sample (0: skip)")
     ap.add_argument("--ref-n", type=int, default=128)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-grid batched launch")
+    ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--tune-rounds", type=int, default=0, help="autotuner rounds (0: until one candidate is left)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

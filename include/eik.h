@@ -235,6 +235,123 @@ eik_status eik_mlp_adam(float *w, const float *grad, float *m, float *v, int32_t
 const char *eik_mlp_last_error(void);
 
 /*
+ * Batched solves -- no counterpart in the paper, which solves one grid at a
+ * time.  Many independent grids, each with its own size, spacing, speed and
+ * sources, are solved by one cooperative persistent launch: each restart
+ * hands out one work queue holding the active blocks of every grid, all grids
+ * share one grid barrier per restart, and grid s runs Alg. 6 with its own
+ * block edge and stride (bound of restart k = k * stride_s).  Each grid gets
+ * the solution eik_solve gives it (the schedule changes which restart does
+ * which work, not the discrete solution).
+ */
+typedef struct eik_batch eik_batch;
+
+typedef struct {
+    int32_t dims[3];        /* nx, ny, nz >= 1; nx*ny*nz < 2^31 */
+    double h;               /* grid spacing, finite and > 0 */
+    const void *F;          /* nx*ny*nz speeds in the batch precision, x fastest, finite and >= 0; copied */
+    int32_t F_on_device;    /* non-zero: F is device memory */
+    int32_t nsrc;           /* >= 1 point sources */
+    const double *xyz;      /* nsrc*3 physical coordinates in host memory, as in eik_add_sources */
+} eik_batch_item;
+
+typedef struct {
+    int32_t block_dim;      /* block edge of the grid: 8 or 16 */
+    double stride;          /* bound increment of the grid: finite and > 0 */
+} eik_batch_tile;
+
+typedef struct {
+    int32_t ctas_per_sm;    /* CTAs per SM of the launch: 0 = the autotuned value, else the most that fit */
+    double window;          /* as eik_params.window (0 = 2) */
+    double fallback_tau;    /* as eik_params.fallback_tau (0 = 1/8) */
+    int64_t max_restarts;   /* restart cap of the launch (0 = 1 << 24) */
+    void *loop_events[2];   /* optional cudaEvent_t pair recorded right before and after the launch */
+} eik_batch_params;
+
+typedef struct {
+    int64_t restarts;       /* restarts of the launch: the most any grid needed */
+    int64_t marches;        /* block marches, summed over grids (a 16^3 block counts 8) */
+    int64_t accepted;       /* band points accepted, summed over grids */
+    int64_t solves;         /* upwind solves (Alg. 3), summed over grids */
+    int64_t updates;        /* solves that lowered psi */
+    int64_t fallbacks;      /* FP32 roots recomputed in double */
+    int64_t rounds;         /* acceptance rounds */
+    double device_ms;       /* device time of the launch (%globaltimer) */
+    int32_t status;         /* eik_status of the device run */
+    int32_t ctas;           /* CTAs of the launch */
+} eik_batch_stats;
+
+typedef struct {
+    int32_t restarts;       /* last restart in which a block of this grid marched */
+    int32_t block_dim;      /* block edge used */
+    double stride;          /* stride used */
+    double done_ms;         /* device time from the start of the launch to the end of that restart:
+                               the grid's latency inside the batch */
+    double rmin;            /* smallest h/F over the grid (the autotuner scales strides by it) */
+    int64_t nbricks;        /* 8^3 bricks of the grid */
+} eik_batch_solve_info;
+
+/*
+ * eik_batch_create -- lay out n grids (items) for batched solves.
+ *   Speeds are copied into the batch; sources are set up once (Alg. 1).
+ *   precision and stream as in eik_create.
+ * Errors: EIK_EINVAL (an item's dims, h, F, sources; the message names the
+ * item), EIK_ENOMEM, EIK_ECUDA, EIK_ENOTSUP (no cooperative launch).
+ */
+eik_status eik_batch_create(eik_batch **out, int32_t n, const eik_batch_item *items, eik_precision precision,
+                            void *stream);
+
+/* eik_batch_params_default -- defaults above. */
+void eik_batch_params_default(eik_batch_params *p);
+
+/*
+ * eik_batch_solve -- solve every grid of the batch in one launch and wait.
+ *   tiles   n tiles (host), or NULL: the autotuned tiles if eik_batch_autotune
+ *           ran, else block edge 8 and stride 2h for every grid.
+ *   params  nullable (defaults).   stats  nullable.
+ * Errors: EIK_EINVAL (a bad tile or parameter), EIK_ETIMEOUT (restart cap or a
+ * device wait limit), EIK_ESTATE (a solve in flight).
+ */
+eik_status eik_batch_solve(eik_batch *b, const eik_batch_tile *tiles, const eik_batch_params *params,
+                           eik_batch_stats *stats);
+
+/* eik_batch_solve_async / eik_batch_wait -- the same, split into queueing and waiting. */
+eik_status eik_batch_solve_async(eik_batch *b, const eik_batch_tile *tiles, const eik_batch_params *params);
+eik_status eik_batch_wait(eik_batch *b, eik_batch_stats *stats);
+
+/* eik_batch_info -- per-grid record of the last solve into out[0..n-1] (host, cap >= n). */
+eik_status eik_batch_info(eik_batch *b, eik_batch_solve_info *out, int32_t cap);
+
+/* eik_batch_result -- psi of grid i (as eik_result: nx*ny*nz, batch precision, x fastest). */
+eik_status eik_batch_result(eik_batch *b, int32_t i, void *psi_out, int out_on_device);
+
+/*
+ * eik_batch_autotune -- pick the tiles and CTAs per SM of this batch by timing
+ * it on the device (each run is a full eik_batch_solve).  Candidates: stride
+ * factor f in {0.5, 0.75, 1, 1.5, 2} (stride of grid s = f * edge_s * rmin_s,
+ * rmin_s = min h/F), block edge 16 for the grids with at least m bricks,
+ * m in {never, 2048, 512, 0}, and every CTAs-per-SM count that fits.  Search:
+ * successive halving -- time every candidate once, keep the best third, time
+ * the survivors twice as often, and so on until one is left (at most `rounds`
+ * rounds; 0 = no limit).  The winner is kept in the batch for later solves
+ * given tiles = NULL and ctas_per_sm = 0, and returned in tiles_out (n tiles,
+ * nullable), ctas_per_sm (nullable) and best_ms (its median device time,
+ * nullable).  The batch's psi afterwards is that of the last timed run.
+ */
+eik_status eik_batch_autotune(eik_batch *b, int32_t rounds, eik_batch_tile *tiles_out, int32_t *ctas_per_sm,
+                              double *best_ms);
+
+/* eik_batch_size -- number of grids, total 8^3 bricks, most CTAs per SM the launch can use (all nullable). */
+eik_status eik_batch_size(const eik_batch *b, int32_t *n, int64_t *nbricks, int32_t *max_ctas_per_sm);
+
+/* eik_batch_destroy -- free the batch (NULL is a no-op). */
+void eik_batch_destroy(eik_batch *b);
+
+/* eik_batch_last_error -- message of the last failure on b (or of the calling thread's last failed
+ * eik_batch_create when b is NULL). */
+const char *eik_batch_last_error(const eik_batch *b);
+
+/*
  * eik_solve_noalloc -- one complete solve that allocates no device memory.
  *
  * No counterpart in the paper: this is a deployment entry point.  It serves

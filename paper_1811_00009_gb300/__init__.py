@@ -62,6 +62,31 @@ class eik_restart_rec(C.Structure):
                 ("features", C.c_float * SCHED_INPUTS)]
 
 
+class eik_batch_item(C.Structure):
+    _fields_ = [("dims", C.c_int32 * 3), ("h", C.c_double), ("F", C.c_void_p), ("F_on_device", C.c_int32),
+                ("nsrc", C.c_int32), ("xyz", C.POINTER(C.c_double))]
+
+
+class eik_batch_tile(C.Structure):
+    _fields_ = [("block_dim", C.c_int32), ("stride", C.c_double)]
+
+
+class eik_batch_params(C.Structure):
+    _fields_ = [("ctas_per_sm", C.c_int32), ("window", C.c_double), ("fallback_tau", C.c_double),
+                ("max_restarts", C.c_int64), ("loop_events", C.c_void_p * 2)]
+
+
+class eik_batch_stats(C.Structure):
+    _fields_ = [("restarts", C.c_int64), ("marches", C.c_int64), ("accepted", C.c_int64), ("solves", C.c_int64),
+                ("updates", C.c_int64), ("fallbacks", C.c_int64), ("rounds", C.c_int64),
+                ("device_ms", C.c_double), ("status", C.c_int32), ("ctas", C.c_int32)]
+
+
+class eik_batch_solve_info(C.Structure):
+    _fields_ = [("restarts", C.c_int32), ("block_dim", C.c_int32), ("stride", C.c_double),
+                ("done_ms", C.c_double), ("rmin", C.c_double), ("nbricks", C.c_int64)]
+
+
 _lock = threading.Lock()
 _L = None
 
@@ -119,6 +144,29 @@ def lib():
             L.eik_mlp_adam.argtypes = [fp, fp, fp, fp, i32, C.c_float, C.c_float, C.c_float, C.c_float, i32, vp]
             L.eik_mlp_last_error.restype = C.c_char_p
             L.eik_mlp_last_error.argtypes = []
+            L.eik_batch_create.restype = i32
+            L.eik_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(eik_batch_item), C.c_int, vp]
+            L.eik_batch_params_default.restype = None
+            L.eik_batch_params_default.argtypes = [C.POINTER(eik_batch_params)]
+            L.eik_batch_solve.restype = i32
+            L.eik_batch_solve.argtypes = [vp, C.POINTER(eik_batch_tile), C.POINTER(eik_batch_params),
+                                          C.POINTER(eik_batch_stats)]
+            L.eik_batch_solve_async.restype = i32
+            L.eik_batch_solve_async.argtypes = [vp, C.POINTER(eik_batch_tile), C.POINTER(eik_batch_params)]
+            L.eik_batch_wait.restype = i32
+            L.eik_batch_wait.argtypes = [vp, C.POINTER(eik_batch_stats)]
+            L.eik_batch_info.restype = i32
+            L.eik_batch_info.argtypes = [vp, C.POINTER(eik_batch_solve_info), i32]
+            L.eik_batch_result.restype = i32
+            L.eik_batch_result.argtypes = [vp, i32, vp, C.c_int]
+            L.eik_batch_autotune.restype = i32
+            L.eik_batch_autotune.argtypes = [vp, i32, C.POINTER(eik_batch_tile), C.POINTER(i32), C.POINTER(dbl)]
+            L.eik_batch_size.restype = i32
+            L.eik_batch_size.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]
+            L.eik_batch_destroy.restype = None
+            L.eik_batch_destroy.argtypes = [vp]
+            L.eik_batch_last_error.restype = C.c_char_p
+            L.eik_batch_last_error.argtypes = [vp]
             _L = L
     return _L
 
@@ -363,6 +411,147 @@ class Solver:
         if self.ctx:
             eik_destroy(self.ctx)
             self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- batched solves (many grids, one persistent launch) ----
+
+def _batch_check(status: int, b=None):
+    if status != EIK_OK:
+        m = lib().eik_batch_last_error(b)
+        raise EikError(status, m.decode() if m else "")
+
+
+def _event_ptr(e):
+    return C.c_void_p(e.cuda_event if hasattr(e, "cuda_event") else int(e))
+
+
+class Batch:
+    """Many independent grids solved by one cooperative launch (eik_batch_* of the C ABI).
+
+    grids: sequence of (dims, h, F, sources): dims = (nx, ny, nz), F a numpy
+    array or torch CUDA tensor of shape (nz, ny, nx) in the batch precision,
+    sources an (n, 3) array of physical coordinates.
+    """
+
+    def __init__(self, grids, precision="fp32", stream=None):
+        prec = _precision(precision)
+        dt = np.float32 if prec == EIK_FP32 else np.float64
+        self.precision = precision
+        self.dims = []
+        items = (eik_batch_item * len(grids))()
+        keep = []
+        for i, (dims, h, F, src) in enumerate(grids):
+            ptr, on_dev, k = _buffer(F, dt)
+            n = int(dims[0]) * int(dims[1]) * int(dims[2])
+            if int(np.prod(getattr(k, "shape", (0,)))) != n:
+                raise ValueError(f"grid {i}: F must hold nx*ny*nz values")
+            xyz = np.ascontiguousarray(np.asarray(src, dtype=np.float64).reshape(-1, 3))
+            keep += [k, xyz]
+            items[i].dims[:] = [int(x) for x in dims]
+            items[i].h = float(h)
+            items[i].F = ptr
+            items[i].F_on_device = on_dev
+            items[i].nsrc = len(xyz)
+            items[i].xyz = xyz.ctypes.data_as(C.POINTER(C.c_double))
+            self.dims.append(tuple(int(x) for x in dims))
+        self.b = C.c_void_p()
+        _batch_check(lib().eik_batch_create(C.byref(self.b), len(grids), items, prec, _stream_handle(stream)))
+        self.n = len(grids)
+
+    @staticmethod
+    def _tiles(tiles):
+        if tiles is None:
+            return None
+        arr = (eik_batch_tile * len(tiles))()
+        for i, (bd, stride) in enumerate(tiles):
+            arr[i].block_dim = int(bd)
+            arr[i].stride = float(stride)
+        return arr
+
+    def _params(self, ctas_per_sm=0, window=0.0, fallback_tau=0.0, max_restarts=0, loop_events=None):
+        p = eik_batch_params()
+        lib().eik_batch_params_default(C.byref(p))
+        p.ctas_per_sm = int(ctas_per_sm)
+        if window:
+            p.window = float(window)
+        if fallback_tau:
+            p.fallback_tau = float(fallback_tau)
+        if max_restarts:
+            p.max_restarts = int(max_restarts)
+        if loop_events is not None:
+            p.loop_events[0] = _event_ptr(loop_events[0])
+            p.loop_events[1] = _event_ptr(loop_events[1])
+        return p
+
+    def solve(self, tiles=None, **kw) -> Dict[str, Any]:
+        """Solve every grid; tiles = [(block_dim, stride)] per grid or None (tuned, else 8 and 2h)."""
+        t = self._tiles(tiles)
+        p = self._params(**kw)
+        s = eik_batch_stats()
+        _batch_check(lib().eik_batch_solve(self.b, t, C.byref(p), C.byref(s)), self.b)
+        return {k: getattr(s, k) for k, _ in eik_batch_stats._fields_}
+
+    def solve_async(self, tiles=None, **kw) -> None:
+        t = self._tiles(tiles)
+        p = self._params(**kw)
+        _batch_check(lib().eik_batch_solve_async(self.b, t, C.byref(p)), self.b)
+
+    def wait(self) -> Dict[str, Any]:
+        s = eik_batch_stats()
+        _batch_check(lib().eik_batch_wait(self.b, C.byref(s)), self.b)
+        return {k: getattr(s, k) for k, _ in eik_batch_stats._fields_}
+
+    def info(self) -> List[Dict[str, Any]]:
+        recs = (eik_batch_solve_info * self.n)()
+        _batch_check(lib().eik_batch_info(self.b, recs, self.n), self.b)
+        return [{k: getattr(r, k) for k, _ in eik_batch_solve_info._fields_} for r in recs]
+
+    def result(self, i: int, out=None):
+        if out is None:
+            dt = np.float32 if _precision(self.precision) == EIK_FP32 else np.float64
+            # an index out of range is left to the library to reject
+            out = np.empty(self.dims[i][::-1] if 0 <= i < self.n else (1,), dtype=dt)
+        for dt in (np.float32, np.float64):
+            try:
+                ptr, on_dev, keep = _buffer(out, dt)
+                break
+            except ValueError:
+                continue
+        else:
+            raise ValueError("out must be a contiguous float32/float64 tensor or array")
+        _batch_check(lib().eik_batch_result(self.b, int(i), ptr, on_dev), self.b)
+        return out
+
+    def autotune(self, rounds: int = 0):
+        """Tune tiles and CTAs per SM on the device; returns (tiles, ctas_per_sm, best_ms)."""
+        t = (eik_batch_tile * self.n)()
+        ctas = C.c_int32()
+        ms = C.c_double()
+        _batch_check(lib().eik_batch_autotune(self.b, int(rounds), t, C.byref(ctas), C.byref(ms)), self.b)
+        return [(t[i].block_dim, t[i].stride) for i in range(self.n)], ctas.value, ms.value
+
+    def size(self):
+        """(grids, total 8^3 bricks, most CTAs per SM the launch can use)."""
+        n, nb, mc = C.c_int32(), C.c_int64(), C.c_int32()
+        _batch_check(lib().eik_batch_size(self.b, C.byref(n), C.byref(nb), C.byref(mc)), self.b)
+        return n.value, nb.value, mc.value
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().eik_batch_destroy(self.b)
+            self.b = None
 
     def __enter__(self):
         return self

@@ -1,6 +1,7 @@
 // Internal definitions of libeik (not part of the C ABI).
 //
-// Data layout in HBM (one grid):
+// Data layout in HBM (one grid; a batch of grids concatenates the bricks
+// of its grids, see SolveDesc):
 //   bricks of 8x8x8 nodes, brick b = (bz*BY + by)*BX + bx, node p = (z*8 + y)*8 + x
 //   inside a brick; a ragged last brick per axis is padded with barrier nodes.
 //   rr[b][512]          h/F (+inf: barrier or padding, -1: fixed source node)
@@ -93,6 +94,18 @@ struct RestartRec {            // mirrors eik_restart_rec
     float features[10];
 };
 
+// One grid of a batched launch: its place in the launch's brick and group
+// index spaces, its block edge and its stride (bound of restart k = k*stride).
+struct SolveDesc {
+    int32_t BX, BY, BZ;
+    int32_t boff;              // global index of the grid's first brick
+    int32_t GX, GY, GZ;
+    int32_t goff;              // global index of the grid's first 2x2x2 group
+    int32_t mode;              // block edge: 8 (one warp per brick) or 16 (one CTA per group)
+    int32_t pad;
+    double stride;
+};
+
 template <typename T>
 struct LoopParams {
     int32_t nx, ny, nz;
@@ -124,6 +137,13 @@ struct LoopParams {
     int32_t nmax;              // longest grid axis (feature scale)
     uint32_t seed;             // random schedule seed
     float margin;              // learned schedule: switch action only if predicted cheaper by this much (log)
+    // batched launch only (eik_batch.cu)
+    const SolveDesc* solves;   // per grid
+    const int32_t* bsolve;     // per brick: its grid
+    const int32_t* gsolve;     // per group: its grid
+    int32_t* last_k;           // per grid: last restart in which one of its blocks marched
+    unsigned long long* tend;  // per restart: %globaltimer at its end
+    int64_t tend_cap;
 };
 
 }  // namespace eikg

@@ -1,0 +1,861 @@
+// Device code shared by the restart-loop kernels (one grid, eik_kernels.cu;
+// many grids, eik_batch.cu): the upwind root of Alg. 3, the per-warp shared
+// memory of a march, and March_Narrow_Band (Alg. 4 with Algs. 2, 3 and the
+// ghost exchange of Alg. 5).
+//
+// One warp marches one 8x8x8 block (a "brick").  The brick's psi, h/F and its
+// six ghost faces sit in shared memory; lane L owns the two x-rows
+// (y = L & 7, z = 2*(L >> 3) + {0, 1}) as a 16-bit mask, plus the ghost nodes
+// next to them.  The band (Sec. 2.1 BAND set) is a list of halo indices shared
+// by the warp; a band node's value carries its sign bit set in shared memory
+// so that any lane can tell a tentative value from an accepted (KNOWN) one
+// with one load.
+//
+// Ordered extraction (Alg. 4) is done in rounds: each round takes the band
+// minimum m with a warp reduction and accepts every band node with
+// psi <= min(m + w, bound), w = omega * min(h/F) over the brick; the
+// neighbours of the accepted nodes (Alg. 2) are compacted into a list and
+// re-solved (Alg. 3) 32 at a time.  A lowered node rejoins the band, so an
+// accepted node can be refreshed later exactly as a KNOWN_NEW node of the
+// paper can.  With w = 0 this is the paper's one-node-at-a-time order.
+#pragma once
+
+#include "eik_internal.cuh"
+
+#include <cfloat>
+#include <cstdint>
+
+namespace eikg {
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kRoundCap = 1 << 20;
+
+template <typename T>
+struct Num;
+template <>
+struct Num<float> {
+    static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+};
+template <>
+struct Num<double> {
+    static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000LL); }
+};
+
+__device__ __forceinline__ bool sgn(float v) { return (__float_as_uint(v) >> 31) != 0u; }
+__device__ __forceinline__ bool sgn(double v) {
+    return (static_cast<unsigned long long>(__double_as_longlong(v)) >> 63) != 0ull;
+}
+__device__ __forceinline__ float vabs(float v) { return fabsf(v); }
+__device__ __forceinline__ double vabs(double v) { return fabs(v); }
+__device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 3: the upwind root for sorted upwind values a <= b <= c (b, c may be
+// +inf) and r = h/F.  Alg. 3 solves a x^2 - 2 b x + c = 0 for the id
+// smallest values, growing id while the root exceeds the next value.  Here
+// the same root is written without cancellation: with k admitted values,
+//   x = v_1 + (sum_i (v_i - v_1) + sqrt(D)) / k,
+//   D = k r^2 - sum_{i<j} (v_i - v_j)^2          (Lagrange's identity),
+// whose differences are exact.  Whenever a value is admitted D > r^2 in
+// exact arithmetic, so D < tau*k*r^2 (tau < 1/3) only flags rounding trouble.
+// ---------------------------------------------------------------------------
+// The root never falls below the largest admitted value (causality of the
+// upwind scheme; exact arithmetic guarantees it, rounding could break it by an
+// ulp and let two nodes lower each other forever), hence the fmax clamps.
+__device__ __forceinline__ double upwind_root(double a, double b, double c, double r) {
+    double x = a + r;
+    if (!(x > b)) return x;
+    const double d = b - a;
+    const double r2 = r * r;
+    double D = 2.0 * r2 - d * d;
+    x = fmax(a + (d + sqrt(fmax(D, 0.0))) * 0.5, b);
+    if (!(x > c)) return x;
+    const double e = c - a, g = c - b;
+    D = 3.0 * r2 - (d * d + e * e + g * g);
+    return fmax(a + (d + e + sqrt(fmax(D, 0.0))) / 3.0, c);
+}
+
+__device__ __forceinline__ float upwind_root_f32(float a, float b, float c, float r, float tau, int& fb) {
+    float x = a + r;
+    if (!(x > b)) return x;
+    const float d = b - a;
+    const float r2 = r * r;
+    float D = 2.0f * r2 - d * d;
+    if (!(r2 >= FLT_MIN) || !(D >= tau * 2.0f * r2)) {
+        ++fb;
+        return static_cast<float>(upwind_root(a, b, c, r));
+    }
+    x = fmaxf(a + (d + sqrtf(D)) * 0.5f, b);
+    if (!(x > c)) return x;
+    const float e = c - a, g = c - b;
+    D = 3.0f * r2 - (d * d + e * e + g * g);
+    if (!(D >= tau * 3.0f * r2)) {
+        ++fb;
+        return static_cast<float>(upwind_root(a, b, c, r));
+    }
+    return fmaxf(a + (d + e + sqrtf(D)) / 3.0f, c);
+}
+
+// Bounds arrive as doubles; a float node value v satisfies v <= b exactly when
+// v <= (the largest float <= b), so the FP32 path compares in float (FP64
+// throughput on this part is a small fraction of FP32).
+template <typename T>
+__device__ __forceinline__ T bound_down(double b);
+template <>
+__device__ __forceinline__ float bound_down<float>(double b) { return __double2float_rd(b); }
+template <>
+__device__ __forceinline__ double bound_down<double>(double b) { return b; }
+
+template <typename T>
+struct RootOf;
+template <>
+struct RootOf<float> {
+    static __device__ __forceinline__ float go(float a, float b, float c, float r, float tau, int& fb) {
+        return upwind_root_f32(a, b, c, r, tau, fb);
+    }
+};
+template <>
+struct RootOf<double> {
+    static __device__ __forceinline__ double go(double a, double b, double c, double r, float, int&) {
+        return upwind_root(a, b, c, r);
+    }
+};
+
+// Per-warp shared memory.
+constexpr int kBandCap = 896;      // 512 interior + 384 ghost nodes: every node at most once
+
+template <typename T>
+struct __align__(16) WarpSmem {
+    T psi[1000];            // brick plus one ghost layer, index ((z+1)*10 + (y+1))*10 + (x+1)
+    T r[kBrick];            // h/F, brick index
+    uint16_t band[kBandCap];// the narrow band: halo indices of the pending nodes
+    uint16_t list[kBrick];  // nodes to re-solve in the current round (halo index)
+    uint32_t mark[32];      // one warp: halo bit vector of the nodes accepted in this round;
+                            // group of warps: bit per brick node, neighbour of a node accepted this round
+    uint32_t upd[16];       // bit per brick node: lowered in this march (Upsilon)
+    uint32_t fxob[16];      // bit per brick node: fixed, barrier or padding node (never solved)
+};
+
+__device__ __forceinline__ int halo_of(int p) {
+    const int x = p & 7, y = (p >> 3) & 7, z = p >> 6;
+    return ((z + 1) * 10 + (y + 1)) * 10 + (x + 1);
+}
+
+template <typename T>
+__device__ __forceinline__ void load8_cg(const T* g, T* out);
+template <>
+__device__ __forceinline__ void load8_cg<float>(const float* g, float* out) {
+    const float4 a = __ldcg(reinterpret_cast<const float4*>(g));
+    const float4 b = __ldcg(reinterpret_cast<const float4*>(g) + 1);
+    out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+    out[4] = b.x; out[5] = b.y; out[6] = b.z; out[7] = b.w;
+}
+template <>
+__device__ __forceinline__ void load8_cg<double>(const double* g, double* out) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const double2 a = __ldcg(reinterpret_cast<const double2*>(g) + i);
+        out[2 * i] = a.x;
+        out[2 * i + 1] = a.y;
+    }
+}
+template <typename T>
+__device__ __forceinline__ void load8_ro(const T* g, T* out);
+template <>
+__device__ __forceinline__ void load8_ro<float>(const float* g, float* out) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(g));
+    const float4 b = __ldg(reinterpret_cast<const float4*>(g) + 1);
+    out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+    out[4] = b.x; out[5] = b.y; out[6] = b.z; out[7] = b.w;
+}
+template <>
+__device__ __forceinline__ void load8_ro<double>(const double* g, double* out) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(g) + i);
+        out[2 * i] = a.x;
+        out[2 * i + 1] = a.y;
+    }
+}
+template <typename T>
+__device__ __forceinline__ void store8(T* g, const T* v);
+template <>
+__device__ __forceinline__ void store8<float>(float* g, const float* v) {
+    reinterpret_cast<float4*>(g)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4*>(g)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+template <>
+__device__ __forceinline__ void store8<double>(double* g, const double* v) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) reinterpret_cast<double2*>(g)[i] = make_double2(v[2 * i], v[2 * i + 1]);
+}
+template <typename T>
+__device__ __forceinline__ void load2_cg(const T* g, T& a, T& b);
+template <>
+__device__ __forceinline__ void load2_cg<float>(const float* g, float& a, float& b) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(g));
+    a = v.x;
+    b = v.y;
+}
+template <>
+__device__ __forceinline__ void load2_cg<double>(const double* g, double& a, double& b) {
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(g));
+    a = v.x;
+    b = v.y;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_min(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = vmin(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = vmax(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_or64(unsigned long long v) {
+    const unsigned lo = __reduce_or_sync(kFull, static_cast<unsigned>(v));
+    const unsigned hi = __reduce_or_sync(kFull, static_cast<unsigned>(v >> 32));
+    return (static_cast<unsigned long long>(hi) << 32) | lo;
+}
+
+struct MarchAcc {
+    unsigned accepted, band;                 // counted on lane 0
+    int fallbacks;                           // per lane
+    unsigned long long solves, updates, rounds;  // the same on every lane
+    float rmin, rmax;                        // the same on every lane
+};
+
+// Halo index of ghost bit `bit` owned by this lane (see the G layout below).
+__device__ __forceinline__ int ghost_halo(int bit, int y, int z0) {
+    if (bit < 4) {
+        const int z = z0 + (bit & 1);
+        const int x = (bit & 2) ? 9 : 0;                 // x = -1 or x = 8
+        return ((z + 1) * 10 + (y + 1)) * 10 + x;
+    }
+    if (bit < 20) {
+        const int j = bit - 4, x = j & 7, z = z0 + (j >> 3);
+        const int row = (y == 0) ? 0 : 9;                // y = -1 or y = 8
+        return ((z + 1) * 10 + row) * 10 + (x + 1);
+    }
+    const int x = bit - 20;
+    const int plane = (z0 == 0) ? 0 : 9;                 // z = -1 or z = 8
+    return (plane * 10 + (y + 1)) * 10 + (x + 1);
+}
+
+// Face-local element u of face f (x faces: u = z*8+y, y faces: u = z*8+x,
+// z faces: u = y*8+x): halo index of the ghost node beyond face f, and halo
+// index of the brick's own boundary node on face f.
+__device__ __forceinline__ int face_ghost_halo(int f, int u) {
+    const int a = u & 7, c = u >> 3;
+    if (f < 2) return ((c + 1) * 10 + (a + 1)) * 10 + (f == 0 ? 0 : 9);
+    if (f < 4) return ((c + 1) * 10 + (f == 2 ? 0 : 9)) * 10 + (a + 1);
+    return ((f == 4 ? 0 : 9) * 10 + (c + 1)) * 10 + (a + 1);
+}
+__device__ __forceinline__ int face_own_halo(int f, int u) {
+    const int a = u & 7, c = u >> 3;
+    if (f < 2) return ((c + 1) * 10 + (a + 1)) * 10 + (f == 0 ? 1 : 8);
+    if (f < 4) return ((c + 1) * 10 + (f == 2 ? 1 : 8)) * 10 + (a + 1);
+    return ((f == 4 ? 1 : 8) * 10 + (c + 1)) * 10 + (a + 1);
+}
+
+// Where a grid sits in the work space of a launch: its bricks are the global
+// indices [boff, boff + BX*BY*BZ), its 2x2x2 groups [goff, goff + GX*GY*GZ).
+// One grid per launch has boff = goff = 0.
+struct Geo {
+    int32_t BX, BY, BZ;
+    int32_t boff;
+    int32_t GX, GY;
+    int32_t goff;
+    uint32_t lists;            // bit 0: keep the brick work list; bit 1: keep the group work list
+};
+
+// Put brick x (global index; and, if the group work list is kept, its group)
+// on restart k+1's work lists, once per restart (the "queued" marks dedupe).
+template <typename T>
+__device__ __forceinline__ void enqueue_next(const LoopParams<T>& P, const Geo& G, int k, int32_t x) {
+    const int par = (k + 1) & 1;
+    if ((G.lists & 1u) && atomicMax(P.queued + x, k + 1) < k + 1) {
+        const int pos = atomicAdd(&P.ctrl->count[par], 1);
+        (par ? P.list1 : P.list0)[pos] = x;
+    }
+    if (!(G.lists & 2u)) return;
+    const int xl = x - G.boff;
+    const int bx = xl % G.BX, by = (xl / G.BX) % G.BY, bz = xl / (G.BX * G.BY);
+    const int32_t g = G.goff + ((bz >> 1) * G.GY + (by >> 1)) * G.GX + (bx >> 1);
+    if (atomicMax(P.qgroup + g, k + 1) < k + 1) {
+        const int pos = atomicAdd(&P.ctrl->gcount[par], 1);
+        (par ? P.glist1 : P.glist0)[pos] = g;
+    }
+}
+
+// March_Narrow_Band (Alg. 4) of brick b at restart k, with the exchange of
+// Alg. 5 for its ghost layer done first from the neighbours' copies as of the
+// end of restart k-1.
+//
+// GROUP = false: one warp, one 8^3 block.  GROUP = true: the eight warps of the
+// CTA march the 2x2x2 bricks of one 16^3 block together (warp w holds brick
+// (w & 1, (w >> 1) & 1, w >> 2) of the group; b < 0 for a brick outside the
+// grid, whose warp only takes part in the barriers).  The rounds then share
+// one acceptance threshold, an accepted node marks the neighbouring warp's
+// nodes across internal faces, and after every phase each warp refreshes its
+// ghost layer on internal faces from the neighbouring warp's tile, so
+// information crosses the internal faces within the restart as it does inside
+// one block of the paper.
+template <typename T, bool GROUP>
+__device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int warp, int32_t b, unsigned gmask,
+                      int k, double bprev_d, double bound_d, double window, int lane, MarchAcc& acc) {
+    __shared__ double s_wmin[kWarps];
+    WarpSmem<T>& S = SW[warp];
+    const T INF = Num<T>::inf();
+    const T bprev = bound_down<T>(bprev_d);
+    const T bound = bound_down<T>(bound_d);
+    const bool present = b >= 0;
+    const int y = lane & 7, zp = lane >> 3, z0 = 2 * zp;
+    const int BX = G.BX, BY = G.BY, BZ = G.BZ;
+    const int bb = present ? b : G.boff;                         // global index; coordinates are local
+    const int bl = bb - G.boff;
+    const int bx = bl % BX, by = (bl / BX) % BY, bz = bl / (BX * BY);
+    const int pbase = (z0 * 8 + y) * 8;                          // brick index of (0, y, z0)
+    const int hbase = ((z0 + 1) * 10 + (y + 1)) * 10 + 1;       // halo index of (0, y, z0)
+    const unsigned lt = (1u << lane) - 1u;
+
+    int nbr[6];
+    nbr[0] = bx > 0 ? bb - 1 : -1;
+    nbr[1] = bx < BX - 1 ? bb + 1 : -1;
+    nbr[2] = by > 0 ? bb - BX : -1;
+    nbr[3] = by < BY - 1 ? bb + BX : -1;
+    nbr[4] = bz > 0 ? bb - BX * BY : -1;
+    nbr[5] = bz < BZ - 1 ? bb + BX * BY : -1;
+
+    unsigned long long st = kUntouched;
+    unsigned FXOB = 0xFFFFu;
+    T rlo = INF, rhi = 0;
+    int n = 0;
+    if (present) {
+        // ---- load phase 1 (independent loads): stamps of the brick and its six
+        // neighbours, and h/F of this lane's two rows
+        st = __ldcg(P.stamp + b);
+        unsigned long long wst[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) wst[f] = nbr[f] >= 0 ? __ldcg(P.stamp + nbr[f]) : kUntouched;
+        // fixed nodes (r < 0) and barrier/padding nodes (r = +inf) are never solved
+        FXOB = 0;
+        {
+            T row[8];
+            const T* rs = P.rr + static_cast<int64_t>(b) * kBrick;
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                load8_ro(rs + pbase + 64 * s, row);
+                store8(S.r + pbase + 64 * s, row);
+#pragma unroll
+                for (int x = 0; x < 8; ++x) {
+                    const T r = row[x];
+                    if (!(r > 0) || !(r < INF)) FXOB |= 1u << (8 * s + x);
+                    else {
+                        rlo = vmin(rlo, r);
+                        rhi = vmax(rhi, r);
+                    }
+                }
+            }
+        }
+        // ---- load phase 2: the brick's latest copy, and the ghost layer: the
+        // neighbours' faces as of the end of restart k-1 with their Upsilon masks
+        // (Alg. 5).  A neighbour that already marched in this restart is read from
+        // its other copy.
+        unsigned long long fups[6];
+        T fv0[6], fv1[6];
+        const int u = 2 * lane;                                   // face-local index of this lane's pair
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            const unsigned long long w = wst[f];
+            int sl = -1, written = -1;
+            if (w != kUntouched) {
+                if (stamp_latest(w) >= k) {
+                    written = stamp_other(w);
+                    sl = (written == static_cast<int>(kNever)) ? -1 : (stamp_copy(w) ^ 1);
+                } else {
+                    written = stamp_latest(w);
+                    sl = stamp_copy(w);
+                }
+            }
+            fups[f] = (sl >= 0 && written == k - 1)
+                          ? __ldcg(P.ups + (static_cast<int64_t>(nbr[f]) * 2 + sl) * 6 + (f ^ 1))
+                          : 0ull;
+            fv0[f] = INF;
+            fv1[f] = INF;
+            if (sl >= 0) {
+                const T* src = P.slot + (static_cast<int64_t>(nbr[f]) * 2 + sl) * kSlot;
+                int off;
+                if (f == 0) off = kXF7 + u;
+                else if (f == 1) off = kXF0 + u;
+                else if (f == 2) off = ((u >> 3) * 8 + 7) * 8 + (u & 7);
+                else if (f == 3) off = ((u >> 3) * 8 + 0) * 8 + (u & 7);
+                else if (f == 4) off = 7 * 64 + u;
+                else off = u;
+                load2_cg(src + off, fv0[f], fv1[f]);
+            }
+        }
+        {
+            T row[8];
+            if (st == kUntouched) {
+#pragma unroll
+                for (int x = 0; x < 8; ++x) S.psi[hbase + x] = INF, S.psi[hbase + 100 + x] = INF;
+            } else {
+                const T* src = P.slot + (static_cast<int64_t>(b) * 2 + stamp_copy(st)) * kSlot;
+                T row1[8];
+                load8_cg(src + pbase, row);
+                load8_cg(src + pbase + 64, row1);
+#pragma unroll
+                for (int x = 0; x < 8; ++x) S.psi[hbase + x] = row[x], S.psi[hbase + 100 + x] = row1[x];
+            }
+        }
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            const int h0 = face_ghost_halo(f, u);
+            S.psi[h0] = fv0[f];
+            S.psi[h0 + (f < 2 ? 10 : 1)] = fv1[f];
+        }
+        __syncwarp();
+
+        // ---- the band at the start of the march: finite nodes above the previous
+        // bound, plus ghost nodes the neighbour lowered in restart k-1 (Upsilon)
+        unsigned B = 0, G = 0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int hh = hbase + (j >> 3) * 100 + (j & 7);
+            const T v = S.psi[hh];
+            if (v < INF && v > bprev) {
+                B |= 1u << j;
+                S.psi[hh] = -v;
+            }
+        }
+        auto mark_ghost = [&](int bit, unsigned long long um, int uu) {
+            const int hh = ghost_halo(bit, y, z0);
+            const T g = S.psi[hh];
+            if (g < INF && (((um >> uu) & 1ull) || g > bprev)) {
+                G |= 1u << bit;
+                S.psi[hh] = -g;
+            }
+        };
+        mark_ghost(0, fups[0], z0 * 8 + y);
+        mark_ghost(1, fups[0], (z0 + 1) * 8 + y);
+        mark_ghost(2, fups[1], z0 * 8 + y);
+        mark_ghost(3, fups[1], (z0 + 1) * 8 + y);
+        if (y == 0 || y == 7) {
+            const unsigned long long um = (y == 0) ? fups[2] : fups[3];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) mark_ghost(4 + j, um, (z0 + (j >> 3)) * 8 + (j & 7));
+        }
+        if (zp == 0 || zp == 3) {
+            const unsigned long long um = (zp == 0) ? fups[4] : fups[5];
+#pragma unroll
+            for (int x = 0; x < 8; ++x) mark_ghost(20 + x, um, y * 8 + x);
+        }
+        __syncwarp();
+        // ---- the band as a list shared by the warp (one entry per pending node)
+        const int cnt = __popc(B) + __popc(G);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        n = __shfl_sync(kFull, incl, 31);
+        int off = incl - cnt;
+        for (unsigned m = B; m; m &= m - 1) {
+            const int j = __ffs(m) - 1;
+            S.band[off++] = static_cast<uint16_t>(hbase + (j >> 3) * 100 + (j & 7));
+        }
+        for (unsigned m = G; m; m &= m - 1) S.band[off++] = static_cast<uint16_t>(ghost_halo(__ffs(m) - 1, y, z0));
+    }
+    if (lane < 16) {
+        S.mark[lane] = 0u;
+        S.upd[lane] = 0u;
+        S.fxob[lane] = 0u;
+    }
+    __syncwarp();
+    if (FXOB & 0xFFu) atomicOr(&S.fxob[pbase >> 5], (FXOB & 0xFFu) << (pbase & 31));
+    if (FXOB >> 8) atomicOr(&S.fxob[(pbase + 64) >> 5], (FXOB >> 8) << ((pbase + 64) & 31));
+
+    const T rmin_b = warp_min(rlo);
+    if (present) {
+        acc.rmin = fminf(acc.rmin, static_cast<float>(rmin_b));
+        acc.rmax = fmaxf(acc.rmax, static_cast<float>(warp_max(rhi)));
+    }
+    T w;
+    if constexpr (GROUP) {
+        // one window for the group: omega times the smallest h/F of its bricks
+        if (lane == 0) s_wmin[warp] = static_cast<double>(rmin_b);
+        __syncthreads();
+        double g = s_wmin[0];
+#pragma unroll
+        for (int i = 1; i < kWarps; ++i) g = fmin(g, s_wmin[i]);
+        w = static_cast<T>(window * g);
+        __syncthreads();
+    } else {
+        w = static_cast<T>(window * static_cast<double>(rmin_b));
+    }
+    const float tau = static_cast<float>(P.fallback_tau);
+
+    // ghost layer on internal faces <- the neighbouring warps' boundary nodes
+    auto refresh_internal = [&]() {
+        if constexpr (GROUP) {
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                if (!((gmask >> f) & 1u)) continue;
+                const WarpSmem<T>& NB = SW[warp ^ (1 << (f >> 1))];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int uu = 2 * lane + e;
+                    S.psi[face_ghost_halo(f, uu)] = NB.psi[face_own_halo(f ^ 1, uu)];
+                }
+            }
+            __syncwarp();
+        }
+    };
+
+    // Alg. 3 for each listed node (halo index), 32 at a time; new values land
+    // after the reads.  A lowered node is tagged BAND (Alg. 2) and joins the band
+    // unless it is in it already.  Returns this lane's smallest lowered value.
+    auto solve_list = [&](int total) -> T {
+        T smin = INF;
+        for (int base = 0; base < total; base += 32) {
+            const int idx = base + lane;
+            bool imp = false, known = false;
+            T xn = 0;
+            int hq = 0, q = 0;
+            if (idx < total) {
+                hq = S.list[idx];
+                // brick index of the halo position: z = hq / 100, y = (hq % 100) / 10 (exact for hq < 1000)
+                const int hz = (hq * 41) >> 12, rem = hq - 100 * hz, hy = (rem * 103) >> 10;
+                q = hz * 64 + hy * 8 + (rem - 10 * hy) - 73;
+                const T cur = S.psi[hq];
+                const T c = vabs(cur);
+                known = !sgn(cur);
+                // KNOWN neighbours below the node's current value (Alg. 3's test)
+                auto kn = [&](T v) -> T { return (sgn(v) || !(v < c)) ? INF : v; };
+                T mx = vmin(kn(S.psi[hq - 1]), kn(S.psi[hq + 1]));
+                T my = vmin(kn(S.psi[hq - 10]), kn(S.psi[hq + 10]));
+                T mz = vmin(kn(S.psi[hq - 100]), kn(S.psi[hq + 100]));
+                // reorder psi_1 <= psi_2 <= psi_3
+                T lo = vmin(mx, my), hi = vmax(mx, my);
+                T a0 = vmin(lo, mz);
+                T t1 = vmax(lo, mz);
+                T a1 = vmin(hi, t1), a2 = vmax(hi, t1);
+                if (a0 < INF) {
+                    xn = RootOf<T>::go(a0, a1, a2, S.r[q], tau, acc.fallbacks);
+                    imp = xn < c;
+                }
+            }
+            __syncwarp();
+            const bool add = imp && known;
+            const unsigned am = __ballot_sync(kFull, add);
+            if (imp) {
+                S.psi[hq] = -xn;
+                atomicOr(&S.upd[q >> 5], 1u << (q & 31));
+                smin = vmin(smin, xn);
+            }
+            if (add) S.band[n + __popc(am & lt)] = static_cast<uint16_t>(hq);
+            n += __popc(am);
+            acc.updates += __popc(__ballot_sync(kFull, imp));
+            __syncwarp();
+        }
+        return smin;
+    };
+    // lane-distributed bit set -> S.list (ascending), returns the entry count
+    auto compact = [&](unsigned bits, int first) -> int {
+        const int cnt = __popc(bits);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int off = incl - cnt;
+        for (unsigned m = bits; m; m &= m - 1) S.list[off++] = static_cast<uint16_t>(first + __ffs(m) - 1);
+        __syncwarp();
+        return __shfl_sync(kFull, incl, 31);
+    };
+
+    // ---- rounds of windowed ordered acceptance (Alg. 4)
+    int rounds = 0;
+    if constexpr (GROUP) {
+        for (;;) {
+            T lmin = INF;
+            for (int i = lane; i < n; i += 32) lmin = vmin(lmin, vabs(S.psi[S.band[i]]));
+            T mn = warp_min(lmin);
+            if (lane == 0) s_wmin[warp] = static_cast<double>(mn);
+            __syncthreads();
+            double g = s_wmin[0];
+#pragma unroll
+            for (int i = 1; i < kWarps; ++i) g = fmin(g, s_wmin[i]);
+            mn = static_cast<T>(g);
+            __syncthreads();
+            if (!(mn < INF) || !(mn <= bound)) break;   // band empty, or its minimum above the bound
+            if (++rounds > kRoundCap) {
+                atomicOr(&P.ctrl->status, kStRoundCap);
+                break;
+            }
+            const T thr = vmin(mn + w, bound);
+            // accept (Remove_Min of a window), keep the rest of the band in order,
+            // and mark the accepted nodes' neighbours (Alg. 2), across internal
+            // faces in the neighbouring warp's tile
+            int kept = 0;
+            for (int base = 0; base < n; base += 32) {
+                const int i = base + lane;
+                int hh = 0;
+                bool keep = false, take = false;
+                if (i < n) {
+                    hh = S.band[i];
+                    const T v = vabs(S.psi[hh]);
+                    if (v <= thr) {
+                        take = true;
+                        S.psi[hh] = v;
+                    } else {
+                        keep = true;
+                    }
+                }
+                const unsigned km = __ballot_sync(kFull, keep);
+                const unsigned tm = __ballot_sync(kFull, take);
+                if (keep) S.band[kept + __popc(km & lt)] = static_cast<uint16_t>(hh);
+                kept += __popc(km);
+                if (lane == 0) acc.accepted += __popc(tm);
+                if (take) {
+                    const int px = hh % 10 - 1, py = (hh / 10) % 10 - 1, pz = hh / 100 - 1;
+                    auto cand = [&](int x, int yy, int z) {
+                        const bool ix = static_cast<unsigned>(x) < 8u, iy = static_cast<unsigned>(yy) < 8u,
+                                   iz = static_cast<unsigned>(z) < 8u;
+                        if (ix && iy && iz) {
+                            const int q = (z * 8 + yy) * 8 + x;
+                            atomicOr(&S.mark[q >> 5], 1u << (q & 31));
+                        } else {
+                            int f = -1;
+                            if (!ix && iy && iz) f = (x < 0) ? 0 : 1;
+                            else if (ix && !iy && iz) f = (yy < 0) ? 2 : 3;
+                            else if (ix && iy && !iz) f = (z < 0) ? 4 : 5;
+                            if (f >= 0 && ((gmask >> f) & 1u)) {
+                                const int q = (((z & 7) * 8) + (yy & 7)) * 8 + (x & 7);
+                                atomicOr(&SW[warp ^ (1 << (f >> 1))].mark[q >> 5], 1u << (q & 31));
+                            }
+                        }
+                    };
+                    cand(px - 1, py, pz);
+                    cand(px + 1, py, pz);
+                    cand(px, py - 1, pz);
+                    cand(px, py + 1, pz);
+                    cand(px, py, pz - 1);
+                    cand(px, py, pz + 1);
+                }
+            }
+            n = kept;
+            __syncthreads();
+            refresh_internal();
+            __syncthreads();
+            // candidates (brick bits, 16 per lane) -> list of halo indices; never-solved nodes dropped
+            const unsigned word = S.mark[lane >> 1] & ~S.fxob[lane >> 1];
+            const unsigned wd = (lane & 1) ? (word >> 16) : (word & 0xFFFFu);
+            __syncwarp();
+            if (lane < 16) S.mark[lane] = 0u;
+            const int total = compact(wd, 16 * lane);   // brick indices
+            for (int i = lane; i < total; i += 32) S.list[i] = static_cast<uint16_t>(halo_of(S.list[i]));
+            __syncwarp();
+            acc.solves += total;
+            solve_list(total);
+            __syncthreads();
+            refresh_internal();
+        }
+    } else {
+        // Halo bit vectors, one 32-bit word per lane (bit j of lane L's word is
+        // halo position 32L + j): `solv` marks the nodes that are solved (not
+        // fixed, barrier or padding); S.mark collects each round's accepted
+        // nodes, whose neighbours are the vector shifted by +-1, +-10, +-100.
+        // Every shift lands an interior node's true neighbour or a ghost
+        // position, and ghost positions are not in `solv`.
+        S.mark[lane] = 0u;
+        __syncwarp();
+        {
+            auto put = [&](int h0, unsigned bits) {
+                if (!bits) return;
+                atomicOr(&S.mark[h0 >> 5], bits << (h0 & 31));
+                if ((h0 & 31) > 24) atomicOr(&S.mark[(h0 >> 5) + 1], bits >> (32 - (h0 & 31)));
+            };
+            put(hbase, ~FXOB & 0xFFu);
+            put(hbase + 100, (~FXOB >> 8) & 0xFFu);
+        }
+        __syncwarp();
+        const unsigned solv = S.mark[lane];
+        __syncwarp();
+        S.mark[lane] = 0u;
+        __syncwarp();
+        T lmin = INF;
+        for (int i = lane; i < n; i += 32) lmin = vmin(lmin, vabs(S.psi[S.band[i]]));
+        T mn = warp_min(lmin);
+        for (;;) {
+            if (!(mn < INF) || !(mn <= bound)) break;   // band empty, or its minimum above the bound
+            if (++rounds > kRoundCap) {
+                atomicOr(&P.ctrl->status, kStRoundCap);
+                break;
+            }
+            const T thr = vmin(mn + w, bound);
+            // accept (Remove_Min of a window) and keep the rest of the band in
+            // order, with the minimum of what is kept
+            int kept = 0;
+            T kmin = INF;
+            for (int base = 0; base < n; base += 32) {
+                const int i = base + lane;
+                int hh = 0;
+                bool keep = false, take = false;
+                if (i < n) {
+                    hh = S.band[i];
+                    const T v = vabs(S.psi[hh]);
+                    if (v <= thr) {
+                        take = true;
+                        S.psi[hh] = v;
+                        atomicOr(&S.mark[hh >> 5], 1u << (hh & 31));
+                    } else {
+                        keep = true;
+                        kmin = vmin(kmin, v);
+                    }
+                }
+                const unsigned km = __ballot_sync(kFull, keep);
+                const unsigned tm = __ballot_sync(kFull, take);
+                if (keep) S.band[kept + __popc(km & lt)] = static_cast<uint16_t>(hh);
+                kept += __popc(km);
+                if (lane == 0) acc.accepted += __popc(tm);
+            }
+            n = kept;
+            __syncwarp();
+            // neighbours of the accepted nodes (Alg. 2) that are solved
+            const unsigned W = S.mark[lane];
+            unsigned wm1 = __shfl_up_sync(kFull, W, 1), wm3 = __shfl_up_sync(kFull, W, 3);
+            unsigned wm4 = __shfl_up_sync(kFull, W, 4), wp1 = __shfl_down_sync(kFull, W, 1);
+            unsigned wp3 = __shfl_down_sync(kFull, W, 3), wp4 = __shfl_down_sync(kFull, W, 4);
+            if (lane < 1) wm1 = 0u;
+            if (lane < 3) wm3 = 0u;
+            if (lane < 4) wm4 = 0u;
+            if (lane > 30) wp1 = 0u;
+            if (lane > 28) wp3 = 0u;
+            if (lane > 27) wp4 = 0u;
+            const unsigned d = (__funnelshift_l(wm1, W, 1) | __funnelshift_l(wm1, W, 10) | __funnelshift_l(wm4, wm3, 4) |
+                                __funnelshift_r(W, wp1, 1) | __funnelshift_r(W, wp1, 10) | __funnelshift_r(wp3, wp4, 4)) &
+                               solv;
+            S.mark[lane] = 0u;
+            const int total = compact(d, 32 * lane);
+            acc.solves += total;
+            const T smin = solve_list(total);
+            mn = warp_min(vmin(kmin, smin));
+        }
+    }
+    acc.rounds += rounds;
+    if constexpr (GROUP) __syncthreads();
+    if (!present) return;
+
+    // ---- Upsilon: own face nodes lowered in this march, per face (face-local bit
+    // masks); none on internal faces of a group, whose neighbours saw them live
+    const unsigned U = ((S.upd[pbase >> 5] >> (pbase & 31)) & 0xFFu) |
+                       (((S.upd[(pbase + 64) >> 5] >> ((pbase + 64) & 31)) & 0xFFu) << 8);
+    unsigned long long um[6];
+    um[0] = (static_cast<unsigned long long>(U & 1u) << (z0 * 8 + y)) |
+            (static_cast<unsigned long long>((U >> 8) & 1u) << ((z0 + 1) * 8 + y));
+    um[1] = (static_cast<unsigned long long>((U >> 7) & 1u) << (z0 * 8 + y)) |
+            (static_cast<unsigned long long>((U >> 15) & 1u) << ((z0 + 1) * 8 + y));
+    um[2] = (y == 0) ? (static_cast<unsigned long long>(U & 0xFFFFu) << (z0 * 8)) : 0ull;
+    um[3] = (y == 7) ? (static_cast<unsigned long long>(U & 0xFFFFu) << (z0 * 8)) : 0ull;
+    um[4] = (zp == 0) ? (static_cast<unsigned long long>(U & 0xFFu) << (y * 8)) : 0ull;
+    um[5] = (zp == 3) ? (static_cast<unsigned long long>((U >> 8) & 0xFFu) << (y * 8)) : 0ull;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        um[f] = warp_or64(um[f]);
+        if (GROUP && ((gmask >> f) & 1u)) um[f] = 0ull;
+    }
+
+    // ---- write the other copy, then publish it
+    const int ns = (st == kUntouched) ? 0 : (stamp_copy(st) ^ 1);
+    T* dst = P.slot + (static_cast<int64_t>(b) * 2 + ns) * kSlot;
+    {
+        T row[8];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+#pragma unroll
+            for (int x = 0; x < 8; ++x) row[x] = vabs(S.psi[hbase + 100 * s + x]);
+            store8(dst + pbase + 64 * s, row);
+            dst[kXF0 + (z0 + s) * 8 + y] = row[0];
+            dst[kXF7 + (z0 + s) * 8 + y] = row[7];
+        }
+    }
+    if (lane < 6) P.ups[(static_cast<int64_t>(b) * 2 + ns) * 6 + lane] = um[lane];
+    // No fence: nobody reads this copy before the grid barrier that ends the
+    // restart (a reader that sees the new stamp takes the other copy).
+    if (lane == 0)
+        P.stamp[b] = make_stamp(k, st == kUntouched ? static_cast<int>(kNever) : stamp_latest(st), ns);
+
+    // ---- activation for restart k+1 (A of Alg. 4/5, C of Alg. 4)
+    if (lane == 6 && n > 0) enqueue_next(P, G, k, b);
+    if (lane < 6 && um[lane] != 0ull && nbr[lane] >= 0) enqueue_next(P, G, k, nbr[lane]);
+    if (lane == 0) acc.band += n;
+}
+
+// Grid-wide barrier of a cooperative launch.  Every CTA arrives; the CTA that
+// arrives last runs last() with all its threads (the restart bookkeeping of
+// Alg. 6), then releases the others.  A waiting CTA gives up after wait_limit
+// polls and flags kStWaitTimeout.  Returns false when this CTA gave up.
+template <class F>
+__device__ bool grid_barrier(Ctrl* C, long long wait_limit, F&& last) {
+    __shared__ int s_last;
+    __shared__ int s_ok;
+    __syncthreads();
+    unsigned gen = 0;
+    if (threadIdx.x == 0) {
+        gen = ld_acquire(&C->bar_gen);
+        __threadfence();
+        const unsigned arrived = atomicAdd(&C->bar_count, 1u);
+        s_last = (arrived == gridDim.x - 1);
+        s_ok = 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        if (threadIdx.x == 0) __threadfence();
+        __syncthreads();
+        last();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            C->bar_count = 0;
+            __threadfence();
+            st_release(&C->bar_gen, gen + 1);
+        }
+    } else if (threadIdx.x == 0) {
+        long long it = 0;
+        while (ld_acquire(&C->bar_gen) == gen) {
+            if (++it > wait_limit) {
+                atomicOr(&C->status, kStWaitTimeout);
+                s_ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+}  // namespace eikg

@@ -6,6 +6,7 @@
 // point sources (Alg. 1), run the cooperative restart-loop kernel, restore h/F
 // at the fixed nodes.  Everything runs on the context's stream.
 #include "eik.h"
+#include "eik_host.h"
 #include "eik_internal.cuh"
 #include "eik_mlp.cuh"
 
@@ -307,57 +308,21 @@ eik_status eik_clear_sources(eik_ctx* c) {
 
 namespace {
 
-// Nodes of the cell containing coordinate s along one axis (Alg. 1, "on or
-// adjacent to Gamma"): one node when s is within 1e-9 cells of a node.
-int cell_nodes(double s, double h, int n, int out[2]) {
-    const double t = s / h;
-    const double tn = std::floor(t + 0.5);
-    if (std::fabs(t - tn) <= 1e-9) {
-        out[0] = std::min(std::max(static_cast<int>(tn), 0), n - 1);
-        return 1;
-    }
-    const int i0 = std::min(std::max(static_cast<int>(std::floor(t)), 0), std::max(n - 2, 0));
-    out[0] = i0;
-    out[1] = std::min(i0 + 1, n - 1);
-    return (out[1] == out[0]) ? 1 : 2;
-}
-
-struct FixNode {
-    int32_t b, p;
-    double v;
-};
-
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 template <typename T>
 eik_status queue_solve(eik_ctx* c, const eik_params& P) {
     cudaStream_t s = c->stream;
     // ---- fixed nodes: candidates of every source, with their h/F from the device
-    struct Cand {
-        int i, j, k;
-        double dist;
-    };
-    std::vector<Cand> cand;
+    const eikh::Bricks geo{c->BX, c->BY, c->BZ, 0};
+    std::vector<eikh::Cand> cand;
     const int nsrc = static_cast<int>(c->src.size() / 3);
-    for (int q = 0; q < nsrc; ++q) {
-        const double* xs = &c->src[3 * q];
-        int ci[3][2], cn[3];
-        cn[0] = cell_nodes(xs[0], c->h, c->nx, ci[0]);
-        cn[1] = cell_nodes(xs[1], c->h, c->ny, ci[1]);
-        cn[2] = cell_nodes(xs[2], c->h, c->nz, ci[2]);
-        for (int a = 0; a < cn[2]; ++a)
-            for (int bq = 0; bq < cn[1]; ++bq)
-                for (int d = 0; d < cn[0]; ++d) {
-                    const int i = ci[0][d], j = ci[1][bq], k = ci[2][a];
-                    const double dx = i * c->h - xs[0], dy = j * c->h - xs[1], dz = k * c->h - xs[2];
-                    cand.push_back({i, j, k, std::sqrt(dx * dx + dy * dy + dz * dz)});
-                }
-    }
+    eikh::source_candidates(c->src.data(), nsrc, c->nx, c->ny, c->nz, c->h, geo, cand);
     const int nc = static_cast<int>(cand.size());
     std::vector<int32_t> cb(nc), cp(nc);
     for (int t = 0; t < nc; ++t) {
-        cb[t] = ((cand[t].k >> 3) * c->BY + (cand[t].j >> 3)) * c->BX + (cand[t].i >> 3);
-        cp[t] = ((cand[t].k & 7) * 8 + (cand[t].j & 7)) * 8 + (cand[t].i & 7);
+        cb[t] = cand[t].b;
+        cp[t] = cand[t].p;
     }
     // scratch: candidate tables, then the fixed-node tables
     const size_t need = align_up(nc * 4) * 2 + align_up(nc * 8) + align_up(nc * 4) * 4 + align_up(nc * 8) +
@@ -386,47 +351,12 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
         EIK_CK(c, cudaMemcpyAsync(cr.data(), d_cr, nc * 8, cudaMemcpyDeviceToHost, s));
         EIK_CK(c, cudaStreamSynchronize(s));
     }
-    std::vector<FixNode> fix;
-    for (int t = 0; t < nc; ++t) {
-        double v;
-        if (cand[t].dist == 0.0) v = 0.0;
-        else if (std::isfinite(cr[t]) && cr[t] > 0.0) v = cand[t].dist * cr[t] / c->h;   // distance / F
-        else continue;                                                                   // barrier node
-        fix.push_back({cb[t], cp[t], v});
-    }
-    std::sort(fix.begin(), fix.end(), [](const FixNode& a, const FixNode& b) {
-        return a.b != b.b ? a.b < b.b : (a.p != b.p ? a.p < b.p : a.v < b.v);
-    });
-    std::vector<FixNode> uf;
-    for (const auto& f : fix)
-        if (uf.empty() || uf.back().b != f.b || uf.back().p != f.p) uf.push_back(f);
-    // bricks holding fixed nodes, and the work list of restart 1: those bricks and
-    // the neighbours whose ghost layer holds a fixed node (Alg. 1 runs over Xi^ib)
+    const std::vector<eikh::FixNode> uf = eikh::fixed_nodes(cand, cr, c->h);
     std::vector<int32_t> sb, enq;
-    for (const auto& f : uf) {
-        if (sb.empty() || sb.back() != f.b) sb.push_back(f.b);
-        enq.push_back(f.b);
-        const int x = f.p & 7, y = (f.p >> 3) & 7, z = f.p >> 6;
-        const int bx = f.b % c->BX, by = (f.b / c->BX) % c->BY, bz = f.b / (c->BX * c->BY);
-        if (x == 0 && bx > 0) enq.push_back(f.b - 1);
-        if (x == 7 && bx < c->BX - 1) enq.push_back(f.b + 1);
-        if (y == 0 && by > 0) enq.push_back(f.b - c->BX);
-        if (y == 7 && by < c->BY - 1) enq.push_back(f.b + c->BX);
-        if (z == 0 && bz > 0) enq.push_back(f.b - c->BX * c->BY);
-        if (z == 7 && bz < c->BZ - 1) enq.push_back(f.b + c->BX * c->BY);
-    }
-    std::sort(enq.begin(), enq.end());
-    enq.erase(std::unique(enq.begin(), enq.end()), enq.end());
+    eikh::first_active(uf, geo, sb, enq);
     const bool groups = (P.block_dim == 16) || (P.schedule != EIK_SCHED_FIXED);
     std::vector<int32_t> genq;
-    if (groups) {
-        for (int32_t b : enq) {
-            const int bx = b % c->BX, by = (b / c->BX) % c->BY, bz = b / (c->BX * c->BY);
-            genq.push_back(((bz >> 1) * c->GY + (by >> 1)) * c->GX + (bx >> 1));
-        }
-        std::sort(genq.begin(), genq.end());
-        genq.erase(std::unique(genq.begin(), genq.end()), genq.end());
-    }
+    if (groups) genq = eikh::groups_of(enq, geo, c->GX, c->GY, 0);
     const int nfix = static_cast<int>(uf.size());
     std::vector<int32_t> fb(nfix), fp(nfix);
     std::vector<double> fv(nfix);

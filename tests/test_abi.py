@@ -66,3 +66,36 @@ def test_null_context_calls_fail_cleanly(eik):
     assert L.eik_result(None, None, 0) == eik.EIK_EINVAL
     assert L.eik_add_sources(None, 0, None) == eik.EIK_EINVAL
     L.eik_destroy(None)
+
+
+@pytest.mark.parametrize("case", ["n0", "dims", "h", "nosrc", "outside"])
+def test_batch_create_rejects_bad_items_before_touching_the_device(eik, case):
+    L = eik.lib()
+    F = np.ones(64, np.float32)
+    xyz = np.zeros(3)
+    items = (eik.eik_batch_item * 2)()
+    for it in items:
+        it.dims[:] = [4, 4, 4]
+        it.h = 0.1
+        it.F = C.c_void_p(F.ctypes.data)
+        it.F_on_device = 0
+        it.nsrc = 1
+        it.xyz = xyz.ctypes.data_as(C.POINTER(C.c_double))
+    n = 2
+    if case == "n0":
+        n = 0
+    elif case == "dims":
+        items[1].dims[:] = [4, 0, 4]
+    elif case == "h":
+        items[1].h = float("nan")
+    elif case == "nosrc":
+        items[1].nsrc = 0
+    else:
+        far = np.array([0.0, 0.0, 1.0])
+        items[1].xyz = far.ctypes.data_as(C.POINTER(C.c_double))
+    out = C.c_void_p()
+    st = L.eik_batch_create(C.byref(out), n, items, 0, None)
+    assert st == eik.EIK_EINVAL
+    assert not out.value
+    msg = L.eik_batch_last_error(None).decode()
+    assert msg and (case == "n0" or "item 1" in msg)
