@@ -190,7 +190,10 @@ def batch_bench(eik, synth, steps: int, warmup: int, tune_rounds: int, dev):
     B = eik.Batch(grids, "fp32", stream=stream)
     try:
         t0 = time.perf_counter()
-        tiles, ctas, tune_ms = B.autotune(rounds=tune_rounds)
+        if tune_rounds >= 0:
+            tiles, ctas, tune_ms = B.autotune(rounds=tune_rounds)
+        else:                                        # untuned: the default tiles
+            tiles, ctas, tune_ms = [(8, 2.0 * w.h) for w in ws], 0, None
         tune_s = time.perf_counter() - t0
 
         def timed(tl, ctas_per_sm):
@@ -225,6 +228,35 @@ def batch_bench(eik, synth, steps: int, warmup: int, tune_rounds: int, dev):
             "tiles": {"ctas_per_sm": ctas, "blocks_8": e8, "blocks_16": 64 - e8, "stride_factor": f,
                       "tune_seconds": tune_s, "tune_best_ms": tune_ms},
             "latency": "per grid: device time from the start of the launch to the end of its last restart"}
+
+
+def run_batch(args):
+    """--workload batch: the 64-grid batched launch alone (one line; solves/s)."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1811_00009_gb300 as eik
+    import synth
+    rounds = -1 if args.no_tune else args.tune_rounds
+    with ClockSampler(0) as clk:
+        b = batch_bench(eik, synth, args.steps, args.warmup, rounds, dev)
+    peak, peak_kind = measured_peaks()
+    tuned = b["autotuned"]
+    achieved = ALGO_BYTES_PER_POINT["fp32"] * b["points"] / (tuned["ms_per_batch"] * 1e-3) / 1e9
+    line = {"metric": "batched solves/s (64 grids, edges 32-192, FP32)", "value": tuned["solves_per_s"],
+            "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tuned["ms_per_batch"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "64 grids, per-axis edges from {32,48,...,192}, 1-4 random sources, sines / "
+                                   "layers / GRF speeds, one persistent launch",
+                       "l2": "working set above L2 (about 0.7 GB of h/F and psi copies), no flush"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "k_batch_loop", "peak_kind": peak_kind},
+            "gpu_launches": 3 * args.steps, "clocks": clk.summary(), "batch": b}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_ours(args):
@@ -420,9 +452,14 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-grid batched launch")
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--tune-rounds", type=int, default=0, help="autotuner rounds (0: until one candidate is left)")
+    ap.add_argument("--no-tune", action="store_true", help="batched launch with the default tiles (8^3, 2h)")
+    ap.add_argument("--workload", choices=["c4", "batch"], default="c4",
+                    help="c4: the 1024^3 solve (default); batch: the 64-grid batched launch alone")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 

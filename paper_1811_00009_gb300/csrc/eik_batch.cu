@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_batch_loop(LoopParams<T> P) 
     for (;;) {
         const int k = __ldcg(&C->k);
         const int par = k & 1;
-        MarchAcc acc{0u, 0u, 0, 0ull, 0ull, 0ull, __int_as_float(0x7f800000), 0.0f};
+        MarchAcc acc{0u, 0u, 0, 0u, 0ull, 0ull, __int_as_float(0x7f800000), 0.0f};
         bool any = false;
         // ---- 16^3 blocks: one CTA per group of 2x2x2 bricks
         {
@@ -163,11 +163,12 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_batch_loop(LoopParams<T> P) 
             const unsigned acc_a = __reduce_add_sync(kFull, acc.accepted);
             const unsigned acc_b = __reduce_add_sync(kFull, acc.band);
             const int fb = __reduce_add_sync(kFull, acc.fallbacks);
+            const unsigned upd = __reduce_add_sync(kFull, acc.updates);
             if (lane == 0) {
                 atomicAdd(&C->r_accepted, static_cast<unsigned long long>(acc_a));
                 atomicAdd(&C->r_band, static_cast<unsigned long long>(acc_b));
                 atomicAdd(&C->r_solves, acc.solves);
-                atomicAdd(&C->r_updates, acc.updates);
+                atomicAdd(&C->r_updates, static_cast<unsigned long long>(upd));
                 atomicAdd(&C->r_rounds, acc.rounds);
                 if (fb) atomicAdd(&C->r_fallbacks, static_cast<unsigned long long>(fb));
             }

@@ -44,6 +44,10 @@ __device__ __forceinline__ bool sgn(float v) { return (__float_as_uint(v) >> 31)
 __device__ __forceinline__ bool sgn(double v) {
     return (static_cast<unsigned long long>(__double_as_longlong(v)) >> 63) != 0ull;
 }
+__device__ __forceinline__ unsigned ubits(float v) { return __float_as_uint(v); }
+__device__ __forceinline__ unsigned long long ubits(double v) {
+    return static_cast<unsigned long long>(__double_as_longlong(v));
+}
 __device__ __forceinline__ float vabs(float v) { return fabsf(v); }
 __device__ __forceinline__ double vabs(double v) { return fabs(v); }
 __device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
@@ -91,6 +95,11 @@ __device__ __forceinline__ double upwind_root(double a, double b, double c, doub
     return fmax(a + (d + e + sqrt(fmax(D, 0.0))) / 3.0, c);
 }
 
+// FP32: sqrt(D) as D * rsqrt(D) (the hardware reciprocal square root, a few
+// ulp) and the division by 3 as a product; D >= tau*k*r^2 > 0 on this path
+// (the max guards tau = 0).
+__device__ __forceinline__ float sqrt_f32(float D) { return D * rsqrtf(fmaxf(D, FLT_MIN)); }
+
 __device__ __forceinline__ float upwind_root_f32(float a, float b, float c, float r, float tau, int& fb) {
     float x = a + r;
     if (!(x > b)) return x;
@@ -101,7 +110,7 @@ __device__ __forceinline__ float upwind_root_f32(float a, float b, float c, floa
         ++fb;
         return static_cast<float>(upwind_root(a, b, c, r));
     }
-    x = fmaxf(a + (d + sqrtf(D)) * 0.5f, b);
+    x = fmaxf(a + (d + sqrt_f32(D)) * 0.5f, b);
     if (!(x > c)) return x;
     const float e = c - a, g = c - b;
     D = 3.0f * r2 - (d * d + e * e + g * g);
@@ -109,7 +118,7 @@ __device__ __forceinline__ float upwind_root_f32(float a, float b, float c, floa
         ++fb;
         return static_cast<float>(upwind_root(a, b, c, r));
     }
-    return fmaxf(a + (d + e + sqrtf(D)) / 3.0f, c);
+    return fmaxf(a + (d + e + sqrt_f32(D)) * (1.0f / 3.0f), c);
 }
 
 // Bounds arrive as doubles; a float node value v satisfies v <= b exactly when
@@ -239,9 +248,11 @@ __device__ __forceinline__ unsigned long long warp_or64(unsigned long long v) {
 }
 
 struct MarchAcc {
-    unsigned accepted, band;                 // counted on lane 0
+    unsigned accepted;                       // per lane
+    unsigned band;                           // counted on lane 0
     int fallbacks;                           // per lane
-    unsigned long long solves, updates, rounds;  // the same on every lane
+    unsigned updates;                        // per lane
+    unsigned long long solves, rounds;       // the same on every lane
     float rmin, rmax;                        // the same on every lane
 };
 
@@ -494,8 +505,10 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
         S.fxob[lane] = 0u;
     }
     __syncwarp();
-    if (FXOB & 0xFFu) atomicOr(&S.fxob[pbase >> 5], (FXOB & 0xFFu) << (pbase & 31));
-    if (FXOB >> 8) atomicOr(&S.fxob[(pbase + 64) >> 5], (FXOB >> 8) << ((pbase + 64) & 31));
+    if constexpr (GROUP) {
+        if (FXOB & 0xFFu) atomicOr(&S.fxob[pbase >> 5], (FXOB & 0xFFu) << (pbase & 31));
+        if (FXOB >> 8) atomicOr(&S.fxob[(pbase + 64) >> 5], (FXOB >> 8) << ((pbase + 64) & 31));
+    }
 
     const T rmin_b = warp_min(rlo);
     if (present) {
@@ -552,8 +565,11 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
                 const T cur = S.psi[hq];
                 const T c = vabs(cur);
                 known = !sgn(cur);
-                // KNOWN neighbours below the node's current value (Alg. 3's test)
-                auto kn = [&](T v) -> T { return (sgn(v) || !(v < c)) ? INF : v; };
+                // KNOWN neighbours below the node's current value (Alg. 3's test): as
+                // unsigned bit patterns every KNOWN (sign clear) value orders as its
+                // value and every BAND value (sign set) lies above any KNOWN one
+                const auto cb = ubits(c);
+                auto kn = [&](T v) -> T { return ubits(v) < cb ? v : INF; };
                 T mx = vmin(kn(S.psi[hq - 1]), kn(S.psi[hq + 1]));
                 T my = vmin(kn(S.psi[hq - 10]), kn(S.psi[hq + 10]));
                 T mz = vmin(kn(S.psi[hq - 100]), kn(S.psi[hq + 100]));
@@ -577,7 +593,7 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
             }
             if (add) S.band[n + __popc(am & lt)] = static_cast<uint16_t>(hq);
             n += __popc(am);
-            acc.updates += __popc(__ballot_sync(kFull, imp));
+            acc.updates += imp ? 1u : 0u;
             __syncwarp();
         }
         return smin;
@@ -636,10 +652,9 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
                     }
                 }
                 const unsigned km = __ballot_sync(kFull, keep);
-                const unsigned tm = __ballot_sync(kFull, take);
                 if (keep) S.band[kept + __popc(km & lt)] = static_cast<uint16_t>(hh);
                 kept += __popc(km);
-                if (lane == 0) acc.accepted += __popc(tm);
+                acc.accepted += take ? 1u : 0u;
                 if (take) {
                     const int px = hh % 10 - 1, py = (hh / 10) % 10 - 1, pz = hh / 100 - 1;
                     auto cand = [&](int x, int yy, int z) {
@@ -738,10 +753,9 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
                     }
                 }
                 const unsigned km = __ballot_sync(kFull, keep);
-                const unsigned tm = __ballot_sync(kFull, take);
                 if (keep) S.band[kept + __popc(km & lt)] = static_cast<uint16_t>(hh);
                 kept += __popc(km);
-                if (lane == 0) acc.accepted += __popc(tm);
+                acc.accepted += take ? 1u : 0u;
             }
             n = kept;
             __syncwarp();
