@@ -256,23 +256,6 @@ struct MarchAcc {
     float rmin, rmax;                        // the same on every lane
 };
 
-// Halo index of ghost bit `bit` owned by this lane (see the G layout below).
-__device__ __forceinline__ int ghost_halo(int bit, int y, int z0) {
-    if (bit < 4) {
-        const int z = z0 + (bit & 1);
-        const int x = (bit & 2) ? 9 : 0;                 // x = -1 or x = 8
-        return ((z + 1) * 10 + (y + 1)) * 10 + x;
-    }
-    if (bit < 20) {
-        const int j = bit - 4, x = j & 7, z = z0 + (j >> 3);
-        const int row = (y == 0) ? 0 : 9;                // y = -1 or y = 8
-        return ((z + 1) * 10 + row) * 10 + (x + 1);
-    }
-    const int x = bit - 20;
-    const int plane = (z0 == 0) ? 0 : 9;                 // z = -1 or z = 8
-    return (plane * 10 + (y + 1)) * 10 + (x + 1);
-}
-
 // Face-local element u of face f (x faces: u = z*8+y, y faces: u = z*8+x,
 // z faces: u = y*8+x): halo index of the ghost node beyond face f, and halo
 // index of the brick's own boundary node on face f.
@@ -426,63 +409,41 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
                 load2_cg(src + off, fv0[f], fv1[f]);
             }
         }
-        {
-            T row[8];
-            if (st == kUntouched) {
+        // ---- the band at the start of the march (marked as the values land in
+        // shared memory): the brick's finite nodes above the previous bound, and
+        // the ghost nodes that are above it or that the neighbour lowered in
+        // restart k-1 (Upsilon) -- the heap contents of Alg. 4 after Alg. 5.
+        // Lane L marks its two rows (bits 0-15 of B) and face-local nodes 2L and
+        // 2L+1 of each face (bits 2f and 2f+1 of G).
+        unsigned B = 0, G = 0;
+        if (st == kUntouched) {
 #pragma unroll
-                for (int x = 0; x < 8; ++x) S.psi[hbase + x] = INF, S.psi[hbase + 100 + x] = INF;
-            } else {
-                const T* src = P.slot + (static_cast<int64_t>(b) * 2 + stamp_copy(st)) * kSlot;
-                T row1[8];
-                load8_cg(src + pbase, row);
-                load8_cg(src + pbase + 64, row1);
+            for (int x = 0; x < 8; ++x) S.psi[hbase + x] = INF, S.psi[hbase + 100 + x] = INF;
+        } else {
+            const T* src = P.slot + (static_cast<int64_t>(b) * 2 + stamp_copy(st)) * kSlot;
+            T row[8], row1[8];
+            load8_cg(src + pbase, row);
+            load8_cg(src + pbase + 64, row1);
 #pragma unroll
-                for (int x = 0; x < 8; ++x) S.psi[hbase + x] = row[x], S.psi[hbase + 100 + x] = row1[x];
+            for (int x = 0; x < 8; ++x) {
+                const T v0 = row[x], v1 = row1[x];
+                const bool b0 = v0 < INF && v0 > bprev, b1 = v1 < INF && v1 > bprev;
+                S.psi[hbase + x] = b0 ? -v0 : v0;
+                S.psi[hbase + 100 + x] = b1 ? -v1 : v1;
+                B |= (b0 ? 1u : 0u) << x;
+                B |= (b1 ? 1u : 0u) << (8 + x);
             }
         }
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
             const int h0 = face_ghost_halo(f, u);
-            S.psi[h0] = fv0[f];
-            S.psi[h0 + (f < 2 ? 10 : 1)] = fv1[f];
+            const T g0 = fv0[f], g1 = fv1[f];
+            const bool b0 = g0 < INF && (((fups[f] >> u) & 1ull) || g0 > bprev);
+            const bool b1 = g1 < INF && (((fups[f] >> (u + 1)) & 1ull) || g1 > bprev);
+            S.psi[h0] = b0 ? -g0 : g0;
+            S.psi[h0 + (f < 2 ? 10 : 1)] = b1 ? -g1 : g1;
+            G |= ((b0 ? 1u : 0u) | (b1 ? 2u : 0u)) << (2 * f);
         }
-        __syncwarp();
-
-        // ---- the band at the start of the march: finite nodes above the previous
-        // bound, plus ghost nodes the neighbour lowered in restart k-1 (Upsilon)
-        unsigned B = 0, G = 0;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int hh = hbase + (j >> 3) * 100 + (j & 7);
-            const T v = S.psi[hh];
-            if (v < INF && v > bprev) {
-                B |= 1u << j;
-                S.psi[hh] = -v;
-            }
-        }
-        auto mark_ghost = [&](int bit, unsigned long long um, int uu) {
-            const int hh = ghost_halo(bit, y, z0);
-            const T g = S.psi[hh];
-            if (g < INF && (((um >> uu) & 1ull) || g > bprev)) {
-                G |= 1u << bit;
-                S.psi[hh] = -g;
-            }
-        };
-        mark_ghost(0, fups[0], z0 * 8 + y);
-        mark_ghost(1, fups[0], (z0 + 1) * 8 + y);
-        mark_ghost(2, fups[1], z0 * 8 + y);
-        mark_ghost(3, fups[1], (z0 + 1) * 8 + y);
-        if (y == 0 || y == 7) {
-            const unsigned long long um = (y == 0) ? fups[2] : fups[3];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) mark_ghost(4 + j, um, (z0 + (j >> 3)) * 8 + (j & 7));
-        }
-        if (zp == 0 || zp == 3) {
-            const unsigned long long um = (zp == 0) ? fups[4] : fups[5];
-#pragma unroll
-            for (int x = 0; x < 8; ++x) mark_ghost(20 + x, um, y * 8 + x);
-        }
-        __syncwarp();
         // ---- the band as a list shared by the warp (one entry per pending node)
         const int cnt = __popc(B) + __popc(G);
         int incl = cnt;
@@ -497,7 +458,10 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
             const int j = __ffs(m) - 1;
             S.band[off++] = static_cast<uint16_t>(hbase + (j >> 3) * 100 + (j & 7));
         }
-        for (unsigned m = G; m; m &= m - 1) S.band[off++] = static_cast<uint16_t>(ghost_halo(__ffs(m) - 1, y, z0));
+        for (unsigned m = G; m; m &= m - 1) {
+            const int j = __ffs(m) - 1, f = j >> 1;
+            S.band[off++] = static_cast<uint16_t>(face_ghost_halo(f, u) + ((j & 1) ? (f < 2 ? 10 : 1) : 0));
+        }
     }
     if (lane < 16) {
         S.mark[lane] = 0u;
@@ -734,28 +698,37 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
             const T thr = vmin(mn + w, bound);
             // accept (Remove_Min of a window) and keep the rest of the band in
             // order, with the minimum of what is kept
+            // (the next chunk's entries are loaded before this chunk's stores, which
+            // only touch earlier band slots and the accepted nodes themselves)
             int kept = 0;
             T kmin = INF;
+            int hh = 0;
+            T v = INF;
+            if (lane < n) {
+                hh = S.band[lane];
+                v = vabs(S.psi[hh]);
+            }
             for (int base = 0; base < n; base += 32) {
-                const int i = base + lane;
-                int hh = 0;
-                bool keep = false, take = false;
-                if (i < n) {
-                    hh = S.band[i];
-                    const T v = vabs(S.psi[hh]);
-                    if (v <= thr) {
-                        take = true;
-                        S.psi[hh] = v;
-                        atomicOr(&S.mark[hh >> 5], 1u << (hh & 31));
-                    } else {
-                        keep = true;
-                        kmin = vmin(kmin, v);
-                    }
+                const bool valid = base + lane < n;
+                int hh2 = 0;
+                T v2 = INF;
+                if (base + 32 + lane < n) {
+                    hh2 = S.band[base + 32 + lane];
+                    v2 = vabs(S.psi[hh2]);
                 }
+                const bool take = valid && v <= thr;
+                const bool keep = valid && !take;
+                if (take) {
+                    S.psi[hh] = v;
+                    atomicOr(&S.mark[hh >> 5], 1u << (hh & 31));
+                }
+                if (keep) kmin = vmin(kmin, v);
                 const unsigned km = __ballot_sync(kFull, keep);
                 if (keep) S.band[kept + __popc(km & lt)] = static_cast<uint16_t>(hh);
                 kept += __popc(km);
                 acc.accepted += take ? 1u : 0u;
+                hh = hh2;
+                v = v2;
             }
             n = kept;
             __syncwarp();
