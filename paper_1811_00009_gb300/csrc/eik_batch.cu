@@ -39,14 +39,14 @@ cudaError_t launch_gather_r(int, const int32_t*, const int32_t*, const T*, doubl
 template <typename T>
 cudaError_t launch_result(const T*, const unsigned long long*, T*, int, int, int, int, int, int, cudaStream_t);
 
-// Restart bookkeeping of a batched launch (run by thread 0 of the CTA that
+// Restart bookkeeping of a batched launch (run by lane 0 of the warp that
 // reaches the barrier last): end time of the restart, totals, exit test.
 template <typename T>
 __device__ void batch_restart_end(const LoopParams<T>& P) {
     Ctrl* C = P.ctrl;
     const int k = __ldcg(&C->k);
-    const int par = k & 1;
-    const int n_next = __ldcg(&C->count[par ^ 1]) + __ldcg(&C->gcount[par ^ 1]);
+    const int par = k % kRing, s1 = (k + 1) % kRing;
+    const int n_next = __ldcg(&C->count[s1]) + __ldcg(&C->gcount[s1]);
     const unsigned long long now = globaltimer();
     if (P.tend != nullptr && k - 1 < P.tend_cap) P.tend[k - 1] = now;
     C->marches += static_cast<unsigned long long>(__ldcg(&C->count[par])) +
@@ -62,6 +62,7 @@ __device__ void batch_restart_end(const LoopParams<T>& P) {
     C->r_updates = 0;
     C->r_fallbacks = 0;
     C->r_rounds = 0;
+    C->used[par] = __ldcg(&C->count[par]);
     C->count[par] = 0;
     C->head[par] = 0;
     C->gcount[par] = 0;
@@ -75,6 +76,7 @@ __device__ void batch_restart_end(const LoopParams<T>& P) {
         C->t_end = now;
     } else {
         C->k = k + 1;
+        C->early_now = (P.early && n_next < kEarlyPerWarp * static_cast<int>(gridDim.x) * kWarps) ? 1 : 0;
         C->t_restart = now;
     }
 }
@@ -99,26 +101,29 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_batch_loop(LoopParams<T> P) 
         C->t_begin = t0;
         C->t_restart = t0;
     }
+    MarchAcc acc{0u, 0u, 0, 0u, 0u, 0u, __int_as_float(0x7f800000), 0.0f};
+    bool any = false;
+    int claim = -1;                            // brick-list entry of the next restart claimed while waiting
     for (;;) {
         const int k = __ldcg(&C->k);
-        const int par = k & 1;
-        MarchAcc acc{0u, 0u, 0, 0u, 0ull, 0ull, __int_as_float(0x7f800000), 0.0f};
-        bool any = false;
+        const int s = k % kRing;
+        const bool early_k = P.early && __ldcg(&C->early_now);
+        if (P.early) clear_used_slot(P, k);
         // ---- 16^3 blocks: one CTA per group of 2x2x2 bricks
         {
-            const int n = __ldcg(&C->gcount[par]);
-            const int32_t* list = par ? P.glist1 : P.glist0;
+            const int n = __ldcg(&C->gcount[s]);
             for (;;) {
                 __syncthreads();
                 if (threadIdx.x == 0) {
-                    const int i = atomicAdd(&C->ghead[par], 1);
-                    s_item = (i < n) ? __ldcg(list + i) : -1;
+                    const int i = atomicAdd(&C->ghead[s], 1);
+                    s_item = -1;
+                    if (i < n) s_item = __ldcg(P.glist[s] + i);
                 }
                 __syncthreads();
                 const int g = s_item;
                 if (g < 0) break;
-                const int s = __ldg(P.gsolve + g);
-                const SolveDesc D = P.solves[s];
+                const int sv = __ldg(P.gsolve + g);
+                const SolveDesc D = P.solves[sv];
                 const Geo G{D.BX, D.BY, D.BZ, D.boff, D.GX, D.GY, D.goff, 2u};
                 const int gl = g - D.goff;
                 const int gx = gl % D.GX, gy = (gl / D.GX) % D.GY, gz = gl / (D.GX * D.GY);
@@ -135,48 +140,80 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_batch_loop(LoopParams<T> P) 
                     else if (bz + 1 < D.BZ) gmask |= 32u;
                 }
                 march<T, true>(P, G, SW, warp, b, gmask, k, batch_bound_prev(D, k), batch_bound(D, k), P.window,
-                               lane, acc);
-                if (threadIdx.x == 0) atomicMax(P.last_k + s, k);
+                               lane, acc, early_k);
+                if (threadIdx.x == 0) atomicMax(P.last_k + sv, k);
                 any = true;
             }
         }
-        // ---- 8^3 blocks: one warp per brick
-        {
-            const int n = __ldcg(&C->count[par]);
-            const int32_t* list = par ? P.list1 : P.list0;
-            for (;;) {
-                int i = 0;
-                if (lane == 0) i = atomicAdd(&C->head[par], 1);
+        // ---- 8^3 blocks, one warp per brick: this restart's list, then -- once
+        // arrived at the barrier -- restart k+1's bricks whose neighbourhood has
+        // finished restart k.  One march call site for both.
+        const int n = __ldcg(&C->count[s]);
+        bool waiting = false;
+        unsigned gen = 0;
+        int polls = 0;
+        unsigned nap = 256;
+        for (;;) {
+            int32_t b = -1;
+            int kk = k;
+            if (!waiting) {
+                int i = -1;
+                if (lane == 0) {
+                    if (claim >= 0 && claim < n) i = claim;    // claimed before the entry existed
+                    else {
+                        const int j = atomicAdd(&C->head[s], 1);
+                        if (j < n) i = j;
+                    }
+                }
                 i = __shfl_sync(kFull, i, 0);
-                if (i >= n) break;
-                const int32_t b = __ldcg(list + i);
-                const int s = __ldg(P.bsolve + b);
-                const SolveDesc D = P.solves[s];
-                const Geo G{D.BX, D.BY, D.BZ, D.boff, D.GX, D.GY, D.goff, 1u};
-                march<T, false>(P, G, SW, warp, b, 0u, k, batch_bound_prev(D, k), batch_bound(D, k), P.window,
-                                lane, acc);
-                if (lane == 0) atomicMax(P.last_k + s, k);
-                any = true;
+                claim = -1;
+                if (i >= 0) b = take_entry(P.list[s], i, false, 0, lane);
+                if (b < 0) {
+                    if (any) flush_acc(C, acc, lane);
+                    any = false;
+                    if (barrier_arrive(C, lane, &gen)) {
+                        if (lane == 0) batch_restart_end<T>(P);
+                        barrier_release(C, lane, gen);
+                        break;
+                    }
+                    waiting = true;
+                    continue;
+                }
+            } else {
+                const int st = barrier_poll(C, lane, gen);
+                if (st == 2) return;
+                if (st == 1) break;
+                if (early_k) b = early_entry(C, P.list[(k + 1) % kRing], (k + 1) % kRing, claim, P.wait_limit, lane);
+                if (b >= 0) {
+                    const SolveDesc D = P.solves[__ldg(P.bsolve + b)];
+                    const Geo G{D.BX, D.BY, D.BZ, D.boff, D.GX, D.GY, D.goff, 1u};
+                    if (!wait_ready(P, G, b, k, lane)) b = -2;
+                }
+                if (b == -2) {
+                    if (lane == 0) atomicOr(&C->status, kStWaitTimeout);
+                    return;
+                }
+                if (b < 0) {
+                    if (++polls > P.wait_limit) {
+                        if (lane == 0) atomicOr(&C->status, kStWaitTimeout);
+                        return;
+                    }
+                    __nanosleep(nap);
+                    if (nap < 4096) nap <<= 1;
+                    continue;
+                }
+                kk = k + 1;
+                polls = 0;
+                nap = 256;
             }
+            const int sv = __ldg(P.bsolve + b);
+            const SolveDesc D = P.solves[sv];
+            const Geo G{D.BX, D.BY, D.BZ, D.boff, D.GX, D.GY, D.goff, 1u};
+            march<T, false>(P, G, SW, warp, b, 0u, kk, batch_bound_prev(D, kk), batch_bound(D, kk), P.window, lane,
+                            acc, early_k || kk > k);
+            if (lane == 0) atomicMax(P.last_k + sv, kk);
+            any = true;
         }
-        if (any) {
-            const unsigned acc_a = __reduce_add_sync(kFull, acc.accepted);
-            const unsigned acc_b = __reduce_add_sync(kFull, acc.band);
-            const int fb = __reduce_add_sync(kFull, acc.fallbacks);
-            const unsigned upd = __reduce_add_sync(kFull, acc.updates);
-            if (lane == 0) {
-                atomicAdd(&C->r_accepted, static_cast<unsigned long long>(acc_a));
-                atomicAdd(&C->r_band, static_cast<unsigned long long>(acc_b));
-                atomicAdd(&C->r_solves, acc.solves);
-                atomicAdd(&C->r_updates, static_cast<unsigned long long>(upd));
-                atomicAdd(&C->r_rounds, acc.rounds);
-                if (fb) atomicAdd(&C->r_fallbacks, static_cast<unsigned long long>(fb));
-            }
-        }
-        const bool ok = grid_barrier(C, P.wait_limit, [&]() {
-            if (threadIdx.x == 0) batch_restart_end<T>(P);
-        });
-        if (!ok) return;
         if (__ldcg(&C->done)) return;
     }
 }
@@ -272,12 +309,11 @@ struct eik_batch {
     void* slot = nullptr;
     unsigned long long* ups = nullptr;
     unsigned long long* stamp = nullptr;
-    int32_t* queued = nullptr;
-    int32_t* list0 = nullptr;
-    int32_t* list1 = nullptr;
-    int32_t* qgroup = nullptr;
-    int32_t* glist0 = nullptr;
-    int32_t* glist1 = nullptr;
+    int32_t* queued = nullptr;     // kRing x nbricks (ring slots)
+    int32_t* lists = nullptr;      // kRing x nbricks
+    int32_t* done = nullptr;       // per brick
+    int32_t* qgroup = nullptr;     // kRing x ngroups
+    int32_t* glists = nullptr;     // kRing x ngroups
     eikg::Ctrl* ctrl = nullptr;
     int* err_flag = nullptr;
     eikg::SolveDesc* d_solves = nullptr;
@@ -324,8 +360,8 @@ eik_status bfail(eik_batch* b, eik_status s, const std::string& m) {
     } while (0)
 
 void bfree_all(eik_batch* b) {
-    void* ptrs[] = {b->rr,       b->slot,     b->ups,      b->stamp,  b->queued,  b->list0,   b->list1,
-                    b->qgroup,   b->glist0,   b->glist1,   b->ctrl,   b->err_flag, b->d_solves, b->bsolve,
+    void* ptrs[] = {b->rr,       b->slot,     b->ups,      b->stamp,  b->queued,  b->lists,   b->done,
+                    b->qgroup,   b->glists,   b->ctrl,     b->err_flag, b->d_solves, b->bsolve,
                     b->gsolve,   b->last_k,   b->tend,     b->d_fix_b, b->d_fix_p, b->d_fix_v, b->d_saved_r,
                     b->d_sb,     b->d_enq,    b->d_genq,   b->d_rmin};
     for (void* p : ptrs)
@@ -520,15 +556,19 @@ eik_status batch_queue(eik_batch* b, const std::vector<eik_batch_tile>& tiles, i
         EIKB_CK(b, cudaMemcpyAsync(b->d_genq, genq.data(), genq.size() * 4, cudaMemcpyHostToDevice, s));
     // ---- Alg. 1 for every brick of every grid
     EIKB_CK(b, cudaMemsetAsync(b->stamp, 0xFF, static_cast<size_t>(b->nbricks) * 8, s));
-    EIKB_CK(b, cudaMemsetAsync(b->queued, 0xFF, static_cast<size_t>(b->nbricks) * 4, s));
-    EIKB_CK(b, cudaMemsetAsync(b->qgroup, 0xFF, static_cast<size_t>(b->ngroups) * 4, s));
+    EIKB_CK(b, cudaMemsetAsync(b->queued, 0xFF, eikg::kRing * static_cast<size_t>(b->nbricks) * 4, s));
+    EIKB_CK(b, cudaMemsetAsync(b->lists, 0xFF, eikg::kRing * static_cast<size_t>(b->nbricks) * 4, s));   // empty: -1
+    EIKB_CK(b, cudaMemsetAsync(b->done, 0, static_cast<size_t>(b->nbricks) * 4, s));
+    EIKB_CK(b, cudaMemsetAsync(b->qgroup, 0xFF, eikg::kRing * static_cast<size_t>(b->ngroups) * 4, s));
+    EIKB_CK(b, cudaMemsetAsync(b->glists, 0xFF, eikg::kRing * static_cast<size_t>(b->ngroups) * 4, s));
     EIKB_CK(b, cudaMemsetAsync(b->last_k, 0, static_cast<size_t>(b->n) * 4, s));
     if (b->nfix > 0)
         EIKB_CK(b, eikg::launch_init_sources<T>(b->nfix, b->d_fix_b, b->d_fix_p, b->d_fix_v, b->nsb, b->d_sb,
                                                 static_cast<int>(enq.size()), b->d_enq, static_cast<int>(genq.size()),
-                                                b->d_genq, static_cast<T*>(b->slot), b->ups, b->stamp, b->queued,
-                                                b->qgroup, static_cast<T*>(b->rr), static_cast<T*>(b->d_saved_r),
-                                                b->list1, b->glist1, s));
+                                                b->d_genq, static_cast<T*>(b->slot), b->ups, b->stamp,
+                                                b->queued + b->nbricks, b->qgroup + b->ngroups,
+                                                static_cast<T*>(b->rr), static_cast<T*>(b->d_saved_r),
+                                                b->lists + b->nbricks, b->glists + b->ngroups, s));
     eikg::Ctrl& H = b->host_ctrl;
     std::memset(&H, 0, sizeof(H));
     const bool work = !enq.empty() || !genq.empty();
@@ -537,6 +577,7 @@ eik_status batch_queue(eik_batch* b, const std::vector<eik_batch_tile>& tiles, i
     H.count[1] = static_cast<int32_t>(enq.size());
     H.gcount[1] = static_cast<int32_t>(genq.size());
     H.r_rmin_bits = 0x7f800000u;
+    H.early_now = 1;                          // restart 1 is small (the cells of the sources)
     H.done = work ? 0 : 1;
     EIKB_CK(b, cudaMemcpyAsync(b->ctrl, &H, sizeof(H), cudaMemcpyHostToDevice, s));
     if (work) {
@@ -545,12 +586,16 @@ eik_status batch_queue(eik_batch* b, const std::vector<eik_batch_tile>& tiles, i
         L.ups = b->ups;
         L.stamp = b->stamp;
         L.queued = b->queued;
+        L.done = b->done;
+        L.nbricks = b->nbricks;
+        L.ngroups = b->ngroups;
+        L.early = 1;
         L.rr = static_cast<const T*>(b->rr);
-        L.list0 = b->list0;
-        L.list1 = b->list1;
+        for (int r = 0; r < eikg::kRing; ++r) {
+            L.list[r] = b->lists + r * b->nbricks;
+            L.glist[r] = b->glists + r * b->ngroups;
+        }
         L.qgroup = b->qgroup;
-        L.glist0 = b->glist0;
-        L.glist1 = b->glist1;
         L.ctrl = b->ctrl;
         L.window = P.window;
         L.fallback_tau = P.fallback_tau;
@@ -838,12 +883,11 @@ eik_status eik_batch_create(eik_batch** out, int32_t n, const eik_batch_item* it
         {&b->slot, nbz * 2 * kSlot * b->esz},
         {reinterpret_cast<void**>(&b->ups), nbz * 2 * 6 * 8},
         {reinterpret_cast<void**>(&b->stamp), nbz * 8},
-        {reinterpret_cast<void**>(&b->queued), nbz * 4},
-        {reinterpret_cast<void**>(&b->list0), nbz * 4},
-        {reinterpret_cast<void**>(&b->list1), nbz * 4},
-        {reinterpret_cast<void**>(&b->qgroup), ngz * 4},
-        {reinterpret_cast<void**>(&b->glist0), ngz * 4},
-        {reinterpret_cast<void**>(&b->glist1), ngz * 4},
+        {reinterpret_cast<void**>(&b->queued), eikg::kRing * nbz * 4},
+        {reinterpret_cast<void**>(&b->lists), eikg::kRing * nbz * 4},
+        {reinterpret_cast<void**>(&b->done), nbz * 4},
+        {reinterpret_cast<void**>(&b->qgroup), eikg::kRing * ngz * 4},
+        {reinterpret_cast<void**>(&b->glists), eikg::kRing * ngz * 4},
         {reinterpret_cast<void**>(&b->ctrl), sizeof(eikg::Ctrl)},
         {reinterpret_cast<void**>(&b->err_flag), sizeof(int)},
         {reinterpret_cast<void**>(&b->d_solves), sizeof(eikg::SolveDesc) * n},

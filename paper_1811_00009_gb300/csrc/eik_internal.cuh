@@ -14,12 +14,17 @@
 //                       restart that wrote the other copy (bits 31..1, all ones
 //                       if never), index of the latest copy (bit 0); all ones
 //                       for a brick no march has touched
-//   queued[b]           last restart the brick was put on the work list for
-//   qgroup[g]           the same for the group g of 2x2x2 bricks (16^3 blocks)
+//   queued[s][b]        restart whose work list (ring slot s = restart mod kRing)
+//                       holds the brick; qgroup[s][g] the same for the group g
+//                       of 2x2x2 bricks (16^3 blocks)
+//   done[b]             last restart whose march of the brick has finished
 // A march at restart k reads the brick's latest copy and its neighbours' copies
 // as of the end of restart k-1, and writes the other copy, so no warp ever
 // reads memory written during the same restart: the exchange step of Alg. 5
-// needs no second grid-wide barrier.
+// needs no second grid-wide barrier.  With a fixed stride a warp waiting at
+// the barrier of restart k may march a brick of restart k+1 early, once the
+// brick and its six neighbours have finished their restart-k marches (done[]):
+// it then reads exactly what it would read after the barrier.
 #pragma once
 
 #include <cstdint>
@@ -33,6 +38,8 @@ constexpr int kSlot = 640;         // values per brick copy
 constexpr int kXF0 = 512;          // offset of the x = 0 face inside a copy
 constexpr int kXF7 = 576;          // offset of the x = 7 face
 constexpr int kWarps = 8;          // warps per CTA of the restart loop (one brick per warp)
+constexpr int kRing = 4;           // work lists in flight: restart k's, k+1's, k+2's (early k+1 marches), k-1's (being cleared)
+constexpr int kEarlyPerWarp = 8;   // early work only in restarts with fewer list entries than this per warp
 
 constexpr unsigned long long kUntouched = ~0ull;   // stamp of a brick no march has written
 constexpr unsigned kNever = 0x7fffffffu;           // "other copy never written"
@@ -56,15 +63,21 @@ constexpr int kStRoundCap = 4;     // a march exceeded its round cap
 struct Ctrl {
     unsigned int bar_count;
     unsigned int bar_gen;
+    int32_t pad_bar[30];       // the barrier words in a cache line of their own (polled by waiting warps)
     int32_t k;                 // current restart (1-based)
     int32_t done;
     int32_t status;
-    int32_t count[2];          // brick work-list lengths, by restart parity
-    int32_t head[2];           // next brick work-list entry to hand out
-    int32_t gcount[2];         // group (16^3 block) work-list lengths, by restart parity
-    int32_t ghead[2];          // next group work-list entry to hand out
+    int32_t pad_k[29];
+    int32_t count[kRing];      // brick work-list lengths, by ring slot (restart mod kRing)
+    int32_t pad_count[28];     // (lengths grow by atomics during a restart; heads are claimed apart)
+    int32_t head[kRing];       // next brick work-list entry to hand out
+    int32_t pad_head[28];
+    int32_t used[kRing];       // length a ring slot's list had when its restart ended (cleared to -1 next restart)
+    int32_t gcount[kRing];     // group (16^3 block) work-list lengths, by ring slot
+    int32_t ghead[kRing];      // next group work-list entry to hand out
     int32_t mode;              // block edge of restart k: 8 (one warp per brick) or 16 (one CTA per group)
     int32_t action;            // schedule action of restart k (-1: none yet)
+    int32_t early_now;         // restart k's marches publish done[] and waiting warps may start restart k+1
     double bound;              // bound_band of restart k
     double bound_prev;         // bound_band of restart k-1 (-1 at k = 1)
     double stride;             // stride that produced `bound`
@@ -111,18 +124,20 @@ struct LoopParams {
     int32_t nx, ny, nz;
     int32_t BX, BY, BZ;
     int64_t nbricks;
+    int64_t ngroups;
     T* slot;
     unsigned long long* ups;
     unsigned long long* stamp;
-    int32_t* queued;
+    int32_t* queued;           // kRing x nbricks: queued[s * nbricks + b] = restart of ring slot s holding b
+    int32_t* done;             // per brick: last restart whose march of it finished
     const T* rr;
-    int32_t* list0;
-    int32_t* list1;
+    int32_t* list[kRing];      // brick work lists by ring slot; unused entries are -1
     int32_t GX, GY, GZ;        // groups of 2x2x2 bricks per axis
     int32_t groups;            // non-zero: keep the group work lists (16^3 restarts possible)
-    int32_t* qgroup;           // per group: last restart it was put on the group list for
-    int32_t* glist0;
-    int32_t* glist1;
+    int32_t* qgroup;           // kRing x ngroups, as queued
+    int32_t* glist[kRing];     // group work lists by ring slot
+    int32_t early;             // non-zero: waiting warps may march the next restart's bricks early
+                               // (in restarts with fewer than kEarlyPerWarp list entries per warp)
     Ctrl* ctrl;
     RestartRec* log;
     int64_t log_cap;

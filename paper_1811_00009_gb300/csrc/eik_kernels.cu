@@ -47,145 +47,135 @@ __device__ inline unsigned mix32(unsigned a) {
     return a;
 }
 
-// Grid barrier at the end of restart k.  The CTA arriving last does the
-// restart bookkeeping of Alg. 6 (statistics, exit test, next bound) and, for
-// the learned schedule, evaluates the schedule network with its threads to
-// pick the stride and block edge of restart k+1, before releasing the others.
-// Returns false when this CTA must leave the loop.
+// Bookkeeping at the end of restart k (run by the warp that reaches the barrier
+// last): statistics, exit test and the next bound of Alg. 6 and, for the
+// learned schedule, the schedule network (one hidden unit per lane) picking
+// the stride and block edge of restart k+1.
 template <typename T>
-__device__ bool end_of_restart(const LoopParams<T>& P) {
+__device__ void restart_end(const LoopParams<T>& P, int lane) {
+    static_assert(kHid == 32, "one hidden unit per lane");
     __shared__ float s_x[kIn];
     __shared__ float s_h1[kHid];
     __shared__ float s_h2[kHid];
     __shared__ float s_y[kAct];
     Ctrl* C = P.ctrl;
-    return grid_barrier(C, P.wait_limit, [&]() {
-        if (threadIdx.x == 0) {
-            const int k = __ldcg(&C->k);
-            const int mode = __ldcg(&C->mode);
-            const int par = k & 1;
-            const int n_this = (mode == 16) ? __ldcg(&C->gcount[par]) : __ldcg(&C->count[par]);
-            schedule_features(s_x, static_cast<double>(n_this) * (mode == 16 ? 8 : 1),
-                              static_cast<double>(__ldcg(&C->r_band)), static_cast<double>(__ldcg(&C->r_accepted)),
-                              static_cast<double>(__ldcg(&C->r_solves)),
-                              static_cast<double>(__uint_as_float(__ldcg(&C->r_rmin_bits))),
-                              static_cast<double>(__uint_as_float(__ldcg(&C->r_rmax_bits))), __ldcg(&C->bound),
-                              __ldcg(&C->stride), k, mode, P.h, P.nmax);
+    const int k = __ldcg(&C->k);
+    const int mode = __ldcg(&C->mode);
+    const int s = k % kRing, s1 = (k + 1) % kRing;
+    const int n_this = (mode == 16) ? __ldcg(&C->gcount[s]) : __ldcg(&C->count[s]);
+    if (lane == 0)
+        schedule_features(s_x, static_cast<double>(n_this) * (mode == 16 ? 8 : 1),
+                          static_cast<double>(__ldcg(&C->r_band)), static_cast<double>(__ldcg(&C->r_accepted)),
+                          static_cast<double>(__ldcg(&C->r_solves)),
+                          static_cast<double>(__uint_as_float(__ldcg(&C->r_rmin_bits))),
+                          static_cast<double>(__uint_as_float(__ldcg(&C->r_rmax_bits))), __ldcg(&C->bound),
+                          __ldcg(&C->stride), k, mode, P.h, P.nmax);
+    __syncwarp();
+    if (P.sched == 1 && P.mlp != nullptr) {
+        const float* w = P.mlp;
+        float a = w[kOffB1 + lane];
+        for (int j = 0; j < kIn; ++j) a += w[kOffW1 + lane * kIn + j] * s_x[j];
+        s_h1[lane] = tanhf(a);
+        __syncwarp();
+        a = w[kOffB2 + lane];
+        for (int j = 0; j < kHid; ++j) a += w[kOffW2 + lane * kHid + j] * s_h1[j];
+        s_h2[lane] = tanhf(a);
+        __syncwarp();
+        if (lane < kAct) {
+            a = w[kOffB3 + lane];
+            for (int j = 0; j < kHid; ++j) a += w[kOffW3 + lane * kHid + j] * s_h2[j];
+            s_y[lane] = a;
         }
-        __syncthreads();
-        if (P.sched == 1 && P.mlp != nullptr) {
-            // the schedule network, one neuron per thread, layer by layer
-            const float* w = P.mlp;
-            const int t = threadIdx.x;
-            if (t < kHid) {
-                float a = w[kOffB1 + t];
-                for (int j = 0; j < kIn; ++j) a += w[kOffW1 + t * kIn + j] * s_x[j];
-                s_h1[t] = tanhf(a);
-            }
-            __syncthreads();
-            if (t < kHid) {
-                float a = w[kOffB2 + t];
-                for (int j = 0; j < kHid; ++j) a += w[kOffW2 + t * kHid + j] * s_h1[j];
-                s_h2[t] = tanhf(a);
-            }
-            __syncthreads();
-            if (t < kAct) {
-                float a = w[kOffB3 + t];
-                for (int j = 0; j < kHid; ++j) a += w[kOffW3 + t * kHid + j] * s_h2[j];
-                s_y[t] = a;
-            }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            const int k = __ldcg(&C->k);
-            const int par = k & 1;
-            const int mode = __ldcg(&C->mode);
-            const int n_this = (mode == 16) ? __ldcg(&C->gcount[par]) : __ldcg(&C->count[par]);
-            // the next restart's stride and block edge
-            double next_stride = __ldcg(&C->stride);
-            int next_mode = P.mode_fixed;
-            int action = -1;
-            if (P.sched == 1 && P.mlp != nullptr) {
-                action = 0;
-                for (int a = 1; a < kAct; ++a)
-                    if (s_y[a] < s_y[action]) action = a;           // lowest predicted cost rate
-                const int cur = __ldcg(&C->action);
-                if (cur >= 0 && s_y[cur] - s_y[action] <= P.margin) action = cur;   // not worth a switch
-                if (!(s_y[action] == s_y[action])) action = -1;    // network output unusable: keep the fixed stride
-            } else if (P.sched == 2) {
-                action = static_cast<int>(mix32(P.seed * 0x9e3779b9u + static_cast<unsigned>(k)) % kAct);
-            }
-            if (action >= 0) {
-                next_stride = action_stride_h(action) * P.h;
-                next_mode = action_block(action);
-            }
-            if (!P.groups) next_mode = 8;
-            const int n_next = (next_mode == 16) ? __ldcg(&C->gcount[par ^ 1]) : __ldcg(&C->count[par ^ 1]);
-            const unsigned long long now = globaltimer();
-            const unsigned long long acc_a = __ldcg(&C->r_accepted), acc_band = __ldcg(&C->r_band);
-            const unsigned long long acc_s = __ldcg(&C->r_solves);
-            if (P.log != nullptr && k - 1 < P.log_cap) {
-                RestartRec rec;
-                rec.k = k;
-                rec.active = n_this * (mode == 16 ? 8 : 1);
-                rec.band = static_cast<int64_t>(acc_band);
-                rec.accepted = static_cast<int64_t>(acc_a);
-                rec.solves = static_cast<int64_t>(acc_s);
-                rec.bound = __ldcg(&C->bound);
-                rec.stride = __ldcg(&C->stride);
-                rec.rmin = __uint_as_float(__ldcg(&C->r_rmin_bits));
-                rec.rmax = __uint_as_float(__ldcg(&C->r_rmax_bits));
-                rec.ms = static_cast<double>(now - __ldcg(&C->t_restart)) * 1e-6;
-                rec.block_dim = mode;
-                rec.next_action = action;
-                for (int i = 0; i < kIn; ++i) rec.features[i] = s_x[i];
-                P.log[k - 1] = rec;
-            }
-            C->marches += static_cast<unsigned long long>(n_this) * (mode == 16 ? 8ull : 1ull);
-            C->accepted += acc_a;
-            C->solves += acc_s;
-            C->updates += __ldcg(&C->r_updates);
-            C->fallbacks += __ldcg(&C->r_fallbacks);
-            C->rounds += __ldcg(&C->r_rounds);
-            C->r_accepted = 0;
-            C->r_band = 0;
-            C->r_solves = 0;
-            C->r_updates = 0;
-            C->r_fallbacks = 0;
-            C->r_rounds = 0;
-            C->r_rmin_bits = 0x7f800000u;
-            C->r_rmax_bits = 0u;
-            C->count[par] = 0;
-            C->head[par] = 0;
-            C->gcount[par] = 0;
-            C->ghead[par] = 0;
-            if (n_next == 0) {
-                C->done = 1;
-                C->t_end = now;
-            } else if (k >= P.max_restarts) {
-                C->done = 1;
-                C->status |= kStRestartCap;
-                C->t_end = now;
-            } else {
-                const double bnd = __ldcg(&C->bound);
-                C->k = k + 1;
-                C->mode = next_mode;
-                C->action = action;
-                C->stride = next_stride;
-                C->bound_prev = bnd;
-                C->bound = bnd + next_stride;               // bound_band <- bound_band + stride (width = +inf)
-                C->t_restart = now;
-            }
-        }
-    });
+        __syncwarp();
+    }
+    if (lane != 0) return;
+    // the next restart's stride and block edge
+    double next_stride = __ldcg(&C->stride);
+    int next_mode = P.mode_fixed;
+    int action = -1;
+    if (P.sched == 1 && P.mlp != nullptr) {
+        action = 0;
+        for (int a = 1; a < kAct; ++a)
+            if (s_y[a] < s_y[action]) action = a;           // lowest predicted cost rate
+        const int cur = __ldcg(&C->action);
+        if (cur >= 0 && s_y[cur] - s_y[action] <= P.margin) action = cur;   // not worth a switch
+        if (!(s_y[action] == s_y[action])) action = -1;    // network output unusable: keep the fixed stride
+    } else if (P.sched == 2) {
+        action = static_cast<int>(mix32(P.seed * 0x9e3779b9u + static_cast<unsigned>(k)) % kAct);
+    }
+    if (action >= 0) {
+        next_stride = action_stride_h(action) * P.h;
+        next_mode = action_block(action);
+    }
+    if (!P.groups) next_mode = 8;
+    const int n_next = (next_mode == 16) ? __ldcg(&C->gcount[s1]) : __ldcg(&C->count[s1]);
+    const unsigned long long now = globaltimer();
+    const unsigned long long acc_a = __ldcg(&C->r_accepted), acc_band = __ldcg(&C->r_band);
+    const unsigned long long acc_s = __ldcg(&C->r_solves);
+    if (P.log != nullptr && k - 1 < P.log_cap) {
+        RestartRec rec;
+        rec.k = k;
+        rec.active = n_this * (mode == 16 ? 8 : 1);
+        rec.band = static_cast<int64_t>(acc_band);
+        rec.accepted = static_cast<int64_t>(acc_a);
+        rec.solves = static_cast<int64_t>(acc_s);
+        rec.bound = __ldcg(&C->bound);
+        rec.stride = __ldcg(&C->stride);
+        rec.rmin = __uint_as_float(__ldcg(&C->r_rmin_bits));
+        rec.rmax = __uint_as_float(__ldcg(&C->r_rmax_bits));
+        rec.ms = static_cast<double>(now - __ldcg(&C->t_restart)) * 1e-6;
+        rec.block_dim = mode;
+        rec.next_action = action;
+        for (int i = 0; i < kIn; ++i) rec.features[i] = s_x[i];
+        P.log[k - 1] = rec;
+    }
+    C->marches += static_cast<unsigned long long>(n_this) * (mode == 16 ? 8ull : 1ull);
+    C->accepted += acc_a;
+    C->solves += acc_s;
+    C->updates += __ldcg(&C->r_updates);
+    C->fallbacks += __ldcg(&C->r_fallbacks);
+    C->rounds += __ldcg(&C->r_rounds);
+    C->r_accepted = 0;
+    C->r_band = 0;
+    C->r_solves = 0;
+    C->r_updates = 0;
+    C->r_fallbacks = 0;
+    C->r_rounds = 0;
+    C->r_rmin_bits = 0x7f800000u;
+    C->r_rmax_bits = 0u;
+    C->used[s] = __ldcg(&C->count[s]);
+    C->count[s] = 0;
+    C->head[s] = 0;
+    C->gcount[s] = 0;
+    C->ghead[s] = 0;
+    if (n_next == 0) {
+        C->done = 1;
+        C->t_end = now;
+    } else if (k >= P.max_restarts) {
+        C->done = 1;
+        C->status |= kStRestartCap;
+        C->t_end = now;
+    } else {
+        const double bnd = __ldcg(&C->bound);
+        C->k = k + 1;
+        C->early_now = (P.early && n_next < kEarlyPerWarp * static_cast<int>(gridDim.x) * kWarps) ? 1 : 0;
+        C->mode = next_mode;
+        C->action = action;
+        C->stride = next_stride;
+        C->bound_prev = bnd;
+        C->bound = bnd + next_stride;               // bound_band <- bound_band + stride (width = +inf)
+        C->t_restart = now;
+    }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
+    __shared__ LoopState s_state[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<T>* SW = reinterpret_cast<WarpSmem<T>*>(smem_raw);
+    LoopState& L = s_state[warp];              // the loop's bookkeeping, kept out of registers
     Ctrl* C = P.ctrl;
     const Geo G{P.BX, P.BY, P.BZ, 0, P.GX, P.GY, 0, 1u | (P.groups ? 2u : 0u)};
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -193,23 +183,34 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P
         C->t_begin = t0;
         C->t_restart = t0;
     }
+    if (lane == 0) L.claim = -1;
+    MarchAcc acc{0u, 0u, 0, 0u, 0u, 0u, __int_as_float(0x7f800000), 0.0f};
+    bool any = false;                          // acc holds something to flush
     for (;;) {
         const int k = __ldcg(&C->k);
-        const double bound = __ldcg(&C->bound);
-        const double bprev = __ldcg(&C->bound_prev);
         const int mode = __ldcg(&C->mode);
-        const int par = k & 1;
-        MarchAcc acc{0u, 0u, 0, 0u, 0ull, 0ull, __int_as_float(0x7f800000), 0.0f};
-        bool any = false;
+        const int s = k % kRing;
+        if (P.early) clear_used_slot(P, k);
+        if (lane == 0) {
+            L.bound = __ldcg(&C->bound);
+            L.bprev = __ldcg(&C->bound_prev);
+            L.next_bound = L.bound + __ldcg(&C->stride);      // restart k+1's bound under a fixed stride
+            L.early = (P.early && __ldcg(&C->early_now) && mode == 8) ? 1 : 0;
+            L.n = (mode == 8) ? __ldcg(&C->count[s]) : 0;
+            L.waiting = 0;
+            L.polls = 0;
+            L.nap = 256;
+        }
+        __syncwarp();
         if (mode == 16) {
             // one CTA per group of 2x2x2 bricks
-            const int n = __ldcg(&C->gcount[par]);
-            const int32_t* list = par ? P.glist1 : P.glist0;
+            const int n = __ldcg(&C->gcount[s]);
             for (;;) {
                 __syncthreads();
                 if (threadIdx.x == 0) {
-                    const int i = atomicAdd(&C->ghead[par], 1);
-                    s_item = (i < n) ? __ldcg(list + i) : -1;
+                    const int i = atomicAdd(&C->ghead[s], 1);
+                    s_item = -1;
+                    if (i < n) s_item = __ldcg(P.glist[s] + i);
                 }
                 __syncthreads();
                 const int g = s_item;
@@ -227,39 +228,84 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P
                     if (warp & 4) gmask |= 16u;
                     else if (bz + 1 < P.BZ) gmask |= 32u;
                 }
-                march<T, true>(P, G, SW, warp, b, gmask, k, bprev, bound, P.window, lane, acc);
+                march<T, true>(P, G, SW, warp, b, gmask, k, L.bprev, L.bound, P.window, lane, acc, L.early != 0);
                 any = true;
             }
-        } else {
-            // one warp per brick
-            const int n = __ldcg(&C->count[par]);
-            const int32_t* list = par ? P.list1 : P.list0;
-            for (;;) {
-                int i = 0;
-                if (lane == 0) i = atomicAdd(&C->head[par], 1);
+        }
+        // One warp per 8^3 brick: this restart's list, then -- once arrived at
+        // the barrier -- restart k+1's bricks whose neighbourhood has finished
+        // restart k (fixed stride and 8^3 blocks only; the next bound is then
+        // known).  One march call site for both.
+        for (;;) {
+            int32_t b = -1;
+            int kk = k;
+            if (!L.waiting) {
+                int i = -1;
+                if (lane == 0) {
+                    const int n = L.n;
+                    if (L.claim >= 0 && L.claim < n) i = L.claim;    // claimed before the entry existed
+                    else {
+                        const int j = atomicAdd(&C->head[s], 1);
+                        if (j < n) i = j;
+                    }
+                    L.claim = -1;
+                }
                 i = __shfl_sync(kFull, i, 0);
-                if (i >= n) break;
-                march<T, false>(P, G, SW, warp, __ldcg(list + i), 0u, k, bprev, bound, P.window, lane, acc);
-                any = true;
+                if (i >= 0) b = take_entry(P.list[s], i, false, 0, lane);
+                if (b < 0) {
+                    if (any) flush_acc(C, acc, lane);
+                    any = false;
+                    unsigned gen;
+                    if (barrier_arrive(C, lane, &gen)) {
+                        restart_end<T>(P, lane);
+                        barrier_release(C, lane, gen);
+                        break;
+                    }
+                    if (lane == 0) {
+                        L.gen = gen;
+                        L.waiting = 1;
+                    }
+                    __syncwarp();
+                    continue;
+                }
+            } else {
+                const int st = barrier_poll(C, lane, L.gen);
+                if (st == 2) return;
+                if (st == 1) break;
+                if (L.early) {
+                    int claim = L.claim;
+                    b = early_entry(C, P.list[(k + 1) % kRing], (k + 1) % kRing, claim, P.wait_limit, lane);
+                    if (lane == 0) L.claim = claim;
+                }
+                if (b >= 0 && !wait_ready(P, G, b, k, lane)) b = -2;
+                if (b == -2) {
+                    if (lane == 0) atomicOr(&C->status, kStWaitTimeout);
+                    return;
+                }
+                if (b < 0) {
+                    int quit = 0;
+                    unsigned nap = 0;
+                    if (lane == 0) {
+                        quit = ++L.polls > P.wait_limit;
+                        nap = L.nap;
+                        if (L.nap < 4096) L.nap <<= 1;
+                        if (quit) atomicOr(&C->status, kStWaitTimeout);
+                    }
+                    if (__shfl_sync(kFull, quit, 0)) return;
+                    __nanosleep(__shfl_sync(kFull, nap, 0));
+                    continue;
+                }
+                kk = k + 1;
+                if (lane == 0) {
+                    L.polls = 0;
+                    L.nap = 256;
+                }
             }
+            __syncwarp();
+            march<T, false>(P, G, SW, warp, b, 0u, kk, kk > k ? L.bound : L.bprev, kk > k ? L.next_bound : L.bound,
+                            P.window, lane, acc, L.early != 0 || kk > k);
+            any = true;
         }
-        if (any) {
-            const unsigned acc_a = __reduce_add_sync(kFull, acc.accepted);
-            const unsigned acc_b = __reduce_add_sync(kFull, acc.band);
-            const int fb = __reduce_add_sync(kFull, acc.fallbacks);
-            const unsigned upd = __reduce_add_sync(kFull, acc.updates);
-            if (lane == 0) {
-                atomicAdd(&C->r_accepted, static_cast<unsigned long long>(acc_a));
-                atomicAdd(&C->r_band, static_cast<unsigned long long>(acc_b));
-                atomicAdd(&C->r_solves, acc.solves);
-                atomicAdd(&C->r_updates, static_cast<unsigned long long>(upd));
-                atomicAdd(&C->r_rounds, acc.rounds);
-                atomicMin(&C->r_rmin_bits, __float_as_uint(acc.rmin));
-                atomicMax(&C->r_rmax_bits, __float_as_uint(acc.rmax));
-                if (fb) atomicAdd(&C->r_fallbacks, static_cast<unsigned long long>(fb));
-            }
-        }
-        if (!end_of_restart<T>(P)) return;
         if (__ldcg(&C->done)) return;
     }
 }

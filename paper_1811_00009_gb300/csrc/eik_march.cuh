@@ -68,6 +68,14 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 // ---------------------------------------------------------------------------
 // Alg. 3: the upwind root for sorted upwind values a <= b <= c (b, c may be
@@ -252,7 +260,7 @@ struct MarchAcc {
     unsigned band;                           // counted on lane 0
     int fallbacks;                           // per lane
     unsigned updates;                        // per lane
-    unsigned long long solves, rounds;       // the same on every lane
+    unsigned solves, rounds;                 // the same on every lane (one restart of one warp)
     float rmin, rmax;                        // the same on every lane
 };
 
@@ -287,18 +295,18 @@ struct Geo {
 // on restart k+1's work lists, once per restart (the "queued" marks dedupe).
 template <typename T>
 __device__ __forceinline__ void enqueue_next(const LoopParams<T>& P, const Geo& G, int k, int32_t x) {
-    const int par = (k + 1) & 1;
-    if ((G.lists & 1u) && atomicMax(P.queued + x, k + 1) < k + 1) {
-        const int pos = atomicAdd(&P.ctrl->count[par], 1);
-        (par ? P.list1 : P.list0)[pos] = x;
+    const int s = (k + 1) % kRing;
+    if ((G.lists & 1u) && atomicMax(P.queued + s * P.nbricks + x, k + 1) < k + 1) {
+        const int pos = atomicAdd(&P.ctrl->count[s], 1);
+        P.list[s][pos] = x;
     }
     if (!(G.lists & 2u)) return;
     const int xl = x - G.boff;
     const int bx = xl % G.BX, by = (xl / G.BX) % G.BY, bz = xl / (G.BX * G.BY);
     const int32_t g = G.goff + ((bz >> 1) * G.GY + (by >> 1)) * G.GX + (bx >> 1);
-    if (atomicMax(P.qgroup + g, k + 1) < k + 1) {
-        const int pos = atomicAdd(&P.ctrl->gcount[par], 1);
-        (par ? P.glist1 : P.glist0)[pos] = g;
+    if (atomicMax(P.qgroup + s * P.ngroups + g, k + 1) < k + 1) {
+        const int pos = atomicAdd(&P.ctrl->gcount[s], 1);
+        P.glist[s][pos] = g;
     }
 }
 
@@ -317,7 +325,7 @@ __device__ __forceinline__ void enqueue_next(const LoopParams<T>& P, const Geo& 
 // one block of the paper.
 template <typename T, bool GROUP>
 __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int warp, int32_t b, unsigned gmask,
-                      int k, double bprev_d, double bound_d, double window, int lane, MarchAcc& acc) {
+                      int k, double bprev_d, double bound_d, double window, int lane, MarchAcc& acc, bool publish) {
     __shared__ double s_wmin[kWarps];
     WarpSmem<T>& S = SW[warp];
     const T INF = Num<T>::inf();
@@ -800,49 +808,160 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
     if (lane == 6 && n > 0) enqueue_next(P, G, k, b);
     if (lane < 6 && um[lane] != 0ull && nbr[lane] >= 0) enqueue_next(P, G, k, nbr[lane]);
     if (lane == 0) acc.band += n;
+    // publish: the brick's restart-k march has finished (read by early marches
+    // of its neighbours; the release store orders the warp's writes above it)
+    if (publish) {
+        __syncwarp();
+        if (lane == 0) st_release(P.done + b, k);
+    }
 }
 
-// Grid-wide barrier of a cooperative launch.  Every CTA arrives; the CTA that
-// arrives last runs last() with all its threads (the restart bookkeeping of
-// Alg. 6), then releases the others.  A waiting CTA gives up after wait_limit
-// polls and flags kStWaitTimeout.  Returns false when this CTA gave up.
-template <class F>
-__device__ bool grid_barrier(Ctrl* C, long long wait_limit, F&& last) {
-    __shared__ int s_last;
-    __shared__ int s_ok;
-    __syncthreads();
-    unsigned gen = 0;
-    if (threadIdx.x == 0) {
-        gen = ld_acquire(&C->bar_gen);
+// Work-list entry i of ring slot s.  An early taker may get an index whose
+// entry is not written yet (the enqueuer bumps the count, then stores): it
+// waits for it (bounded; -1 on timeout).  Unwritten entries are -1: a slot is
+// cleared at the start of the restart after the one that used it
+// (clear_used_slot), before it is used again two restarts later.
+__device__ __forceinline__ int32_t take_entry(const int32_t* list, int i, bool wait, long long limit, int lane) {
+    if (!wait) return __ldcg(list + i);
+    int32_t v = -1;
+    if (lane == 0) {
+        v = ld_acquire(list + i);
+        for (long long it = 0; v < 0 && it < limit; ++it) {
+            __nanosleep(32);
+            v = ld_acquire(list + i);
+        }
+    }
+    return __shfl_sync(0xffffffffu, v, 0);
+}
+
+// At the start of restart k: every thread of the launch clears its share of the
+// brick list restart k-1 used (ring slot (k-1) mod kRing), coalesced.  The
+// slot is next written in restart k+1 (by early marches of restart k+2 while
+// waiting at its barrier) at the earliest, after every warp has arrived at the
+// barrier of restart k and so has finished its share.
+template <typename T>
+__device__ __forceinline__ void clear_used_slot(const LoopParams<T>& P, int k) {
+    const int sp = (k + kRing - 1) % kRing;
+    const int m = __ldcg(&P.ctrl->used[sp]);
+    int32_t* list = P.list[sp];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) list[i] = -1;
+}
+
+// Before an early march of brick b at restart k+1: wait until b and each of its
+// six neighbours that is on restart k's work list has finished that march
+// (bounded; false on timeout).  After it the march reads what it would read
+// after the barrier of restart k.
+template <typename T>
+__device__ bool wait_ready(const LoopParams<T>& P, const Geo& G, int32_t b, int k, int lane) {
+    int32_t x = -1;
+    if (lane < 7) {
+        const int bl = b - G.boff;
+        const int bx = bl % G.BX, by = (bl / G.BX) % G.BY, bz = bl / (G.BX * G.BY);
+        if (lane == 6) x = b;
+        else if (lane == 0) x = bx > 0 ? b - 1 : -1;
+        else if (lane == 1) x = bx < G.BX - 1 ? b + 1 : -1;
+        else if (lane == 2) x = by > 0 ? b - G.BX : -1;
+        else if (lane == 3) x = by < G.BY - 1 ? b + G.BX : -1;
+        else if (lane == 4) x = bz > 0 ? b - G.BX * G.BY : -1;
+        else x = bz < G.BZ - 1 ? b + G.BX * G.BY : -1;
+    }
+    bool need = x >= 0 && __ldcg(P.queued + (k % kRing) * P.nbricks + x) == k;
+    unsigned nap = 128;
+    for (long long it = 0;; ++it) {
+        if (need && ld_acquire(P.done + x) >= k) need = false;
+        if (!__any_sync(0xffffffffu, need)) break;
+        if (it > P.wait_limit) return false;
+        __nanosleep(nap);
+        if (nap < 2048) nap <<= 1;
+    }
+    __syncwarp();
+    return true;
+}
+
+// This warp's statistics of the restart -> the control block.
+__device__ __forceinline__ void flush_acc(Ctrl* C, MarchAcc& acc, int lane) {
+    const unsigned acc_a = __reduce_add_sync(0xffffffffu, acc.accepted);
+    const unsigned acc_b = __reduce_add_sync(0xffffffffu, acc.band);
+    const int fb = __reduce_add_sync(0xffffffffu, acc.fallbacks);
+    const unsigned upd = __reduce_add_sync(0xffffffffu, acc.updates);
+    if (lane == 0) {
+        atomicAdd(&C->r_accepted, static_cast<unsigned long long>(acc_a));
+        atomicAdd(&C->r_band, static_cast<unsigned long long>(acc_b));
+        atomicAdd(&C->r_solves, static_cast<unsigned long long>(acc.solves));
+        atomicAdd(&C->r_updates, static_cast<unsigned long long>(upd));
+        atomicAdd(&C->r_rounds, static_cast<unsigned long long>(acc.rounds));
+        atomicMin(&C->r_rmin_bits, __float_as_uint(acc.rmin));
+        atomicMax(&C->r_rmax_bits, __float_as_uint(acc.rmax));
+        if (fb) atomicAdd(&C->r_fallbacks, static_cast<unsigned long long>(fb));
+    }
+    acc = MarchAcc{0u, 0u, 0, 0u, 0u, 0u, __int_as_float(0x7f800000), 0.0f};
+}
+
+// Per-warp state of the restart loop, in shared memory (lane 0 writes it):
+// the march needs every register it can get.
+struct LoopState {
+    double bound, bprev, next_bound;
+    int n;                     // length of this restart's brick list
+    int early;                 // early work allowed while waiting at this restart's barrier
+    int waiting;               // arrived at the barrier
+    unsigned gen;              // barrier generation to wait past
+    int polls;
+    unsigned nap;
+    int claim;                 // entry of the next restart's list claimed while waiting (-1: none)
+};
+
+// Grid barrier at the end of a restart, one warp at a time: every warp of the
+// launch arrives on its own (lane 0's atomic), and the warp arriving last does
+// the restart bookkeeping and then releases the others by bumping bar_gen.
+// barrier_arrive returns true for that last warp; *gen gets the generation the
+// others wait to see change.
+__device__ __forceinline__ bool barrier_arrive(Ctrl* C, int lane, unsigned* gen) {
+    unsigned g = 0;
+    int last = 0;
+    if (lane == 0) {
+        g = ld_acquire(&C->bar_gen);
         __threadfence();
-        const unsigned arrived = atomicAdd(&C->bar_count, 1u);
-        s_last = (arrived == gridDim.x - 1);
-        s_ok = 1;
+        last = atomicAdd(&C->bar_count, 1u) == gridDim.x * (blockDim.x >> 5) - 1;
+        if (last) __threadfence();
     }
-    __syncthreads();
-    if (s_last) {
-        if (threadIdx.x == 0) __threadfence();
-        __syncthreads();
-        last();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            C->bar_count = 0;
-            __threadfence();
-            st_release(&C->bar_gen, gen + 1);
-        }
-    } else if (threadIdx.x == 0) {
-        long long it = 0;
-        while (ld_acquire(&C->bar_gen) == gen) {
-            if (++it > wait_limit) {
-                atomicOr(&C->status, kStWaitTimeout);
-                s_ok = 0;
-                break;
-            }
-            __nanosleep(64);
-        }
+    *gen = __shfl_sync(0xffffffffu, g, 0);
+    return __shfl_sync(0xffffffffu, last, 0) != 0;
+}
+__device__ __forceinline__ void barrier_release(Ctrl* C, int lane, unsigned gen) {
+    __syncwarp();
+    if (lane == 0) {
+        C->bar_count = 0;
+        __threadfence();
+        st_release(&C->bar_gen, gen + 1);
     }
-    __syncthreads();
-    return s_ok != 0;
+}
+// 1: released; 2: a wait somewhere ran out (kStWaitTimeout); 0: keep waiting.
+__device__ __forceinline__ int barrier_poll(Ctrl* C, int lane, unsigned gen) {
+    int state = 0;
+    if (lane == 0) {
+        if (ld_acquire(&C->bar_gen) != gen) state = 1;
+        else if (__ldcg(&C->status) & kStWaitTimeout) state = 2;
+    }
+    return __shfl_sync(0xffffffffu, state, 0);
+}
+
+// While waiting at the barrier of restart k: the next entry of restart k+1's
+// list (ring slot s1) for an early march, or -1.  A warp claims one index
+// (atomicAdd on the slot's head) and keeps the claim until the list holds that
+// entry; a claim still open at the release is settled by the claimer at the
+// start of restart k+1 (settle_claim).
+__device__ __forceinline__ int32_t early_entry(Ctrl* C, int32_t* list, int s1, int& claim, long long limit,
+                                               int lane) {
+    if (claim < 0) {
+        if (lane == 0) claim = atomicAdd(&C->head[s1], 1);
+        claim = __shfl_sync(0xffffffffu, claim, 0);
+    }
+    int have = 0;
+    if (lane == 0) have = claim < __ldcg(&C->count[s1]);
+    if (!__shfl_sync(0xffffffffu, have, 0)) return -1;
+    const int32_t b = take_entry(list, claim, true, limit, lane);
+    claim = -1;
+    return b < 0 ? -2 : b;
 }
 
 }  // namespace eikg

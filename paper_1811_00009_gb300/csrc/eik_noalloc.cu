@@ -87,7 +87,7 @@ cudaError_t scratch_base(void** out) {
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t rr, slot, ups, stamp, queued, list0, list1, ctrl, err, fix_b, fix_p, fix_v, src_b, enq, saved_r, cand_r,
+    size_t rr, slot, ups, stamp, queued, lists, done, ctrl, err, fix_b, fix_p, fix_v, src_b, enq, saved_r, cand_r,
         end;
 };
 
@@ -103,9 +103,9 @@ Layout layout_for(int64_t nb) {
     L.slot = take(static_cast<size_t>(nb) * 2 * eikg::kSlot * sizeof(float));
     L.ups = take(static_cast<size_t>(nb) * 12 * sizeof(unsigned long long));
     L.stamp = take(static_cast<size_t>(nb) * sizeof(unsigned long long));
-    L.queued = take(static_cast<size_t>(nb) * sizeof(int32_t));
-    L.list0 = take(static_cast<size_t>(nb) * sizeof(int32_t));
-    L.list1 = take(static_cast<size_t>(nb) * sizeof(int32_t));
+    L.queued = take(eikg::kRing * static_cast<size_t>(nb) * sizeof(int32_t));
+    L.lists = take(eikg::kRing * static_cast<size_t>(nb) * sizeof(int32_t));
+    L.done = take(static_cast<size_t>(nb) * sizeof(int32_t));
     L.ctrl = take(sizeof(eikg::Ctrl));
     L.err = take(sizeof(int));
     L.fix_b = take(kMaxFix * sizeof(int32_t));
@@ -178,8 +178,8 @@ eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float* F, in
     auto* ups = reinterpret_cast<unsigned long long*>(B + Lo.ups);
     auto* stampv = reinterpret_cast<unsigned long long*>(B + Lo.stamp);
     int32_t* queued = reinterpret_cast<int32_t*>(B + Lo.queued);
-    int32_t* list0 = reinterpret_cast<int32_t*>(B + Lo.list0);
-    int32_t* list1 = reinterpret_cast<int32_t*>(B + Lo.list1);
+    int32_t* lists = reinterpret_cast<int32_t*>(B + Lo.lists);
+    int32_t* done = reinterpret_cast<int32_t*>(B + Lo.done);
     auto* ctrl = reinterpret_cast<eikg::Ctrl*>(B + Lo.ctrl);
     int* err = reinterpret_cast<int*>(B + Lo.err);
     int32_t* d_fb = reinterpret_cast<int32_t*>(B + Lo.fix_b);
@@ -273,10 +273,13 @@ eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float* F, in
     H.mode = 8;
     H.action = -1;
     H.r_rmin_bits = 0x7f800000u;
+    H.early_now = 1;                          // restart 1 is small (the cells of the sources)
     H.done = nenq ? 0 : 1;
     // state that must start fresh: stamps and work-list marks (all ones), control block
     NA_CK(cudaMemsetAsync(stampv, 0xFF, static_cast<size_t>(nb) * sizeof(unsigned long long), st));
-    NA_CK(cudaMemsetAsync(queued, 0xFF, static_cast<size_t>(nb) * sizeof(int32_t), st));
+    NA_CK(cudaMemsetAsync(queued, 0xFF, eikg::kRing * static_cast<size_t>(nb) * sizeof(int32_t), st));
+    NA_CK(cudaMemsetAsync(lists, 0xFF, eikg::kRing * static_cast<size_t>(nb) * sizeof(int32_t), st));   // empty entries: -1
+    NA_CK(cudaMemsetAsync(done, 0, static_cast<size_t>(nb) * sizeof(int32_t), st));
     NA_CK(cudaMemcpyAsync(ctrl, &H, sizeof(H), cudaMemcpyHostToDevice, st));
     if (nfix > 0) {
         NA_CK(cudaMemcpyAsync(d_fb, fb, nfix * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -285,7 +288,7 @@ eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float* F, in
         NA_CK(cudaMemcpyAsync(d_sb, sb, nsb * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         NA_CK(cudaMemcpyAsync(d_enq, enq, nenq * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         NA_CK(eikg::launch_init_sources<float>(nfix, d_fb, d_fp, d_fv, nsb, d_sb, nenq, d_enq, 0, nullptr, slot, ups,
-                                               stampv, queued, nullptr, rr, d_saved, list1, nullptr, st));
+                                               stampv, queued + nb, nullptr, rr, d_saved, lists + nb, nullptr, st));
     }
     if (nenq > 0) {
         int per_sm = 0, sms = 0, dev = 0;
@@ -305,8 +308,9 @@ eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float* F, in
         L.stamp = stampv;
         L.queued = queued;
         L.rr = rr;
-        L.list0 = list0;
-        L.list1 = list1;
+        L.done = done;
+        for (int r = 0; r < eikg::kRing; ++r) L.list[r] = lists + r * nb;
+        L.early = 1;
         L.groups = 0;                 // 8^3 blocks only: no group work lists
         L.mode_fixed = 8;
         L.ctrl = ctrl;

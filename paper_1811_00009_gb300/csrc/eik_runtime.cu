@@ -54,14 +54,13 @@ struct eik_ctx {
     void* slot = nullptr;
     unsigned long long* ups = nullptr;
     unsigned long long* stamp = nullptr;
-    int32_t* queued = nullptr;
-    int32_t* list0 = nullptr;
-    int32_t* list1 = nullptr;
+    int32_t* queued = nullptr;     // kRing x nbricks (ring slots)
+    int32_t* lists = nullptr;      // kRing x nbricks: the brick work lists by ring slot
+    int32_t* done = nullptr;       // per brick
     int GX = 0, GY = 0, GZ = 0;
     int64_t ngroups = 0;
-    int32_t* qgroup = nullptr;
-    int32_t* glist0 = nullptr;
-    int32_t* glist1 = nullptr;
+    int32_t* qgroup = nullptr;     // kRing x ngroups
+    int32_t* glists = nullptr;     // kRing x ngroups
     eikg::Ctrl* ctrl = nullptr;
     int* err_flag = nullptr;
     float* d_mlp = nullptr;        // schedule network weights (eik_set_schedule)
@@ -110,7 +109,7 @@ cudaError_t dalloc(P** p, size_t bytes) {
 }
 
 void free_all(eik_ctx* c) {
-    void* ptrs[] = {c->rr,    c->slot,  c->ups,   c->stamp,   c->queued, c->list0, c->list1, c->qgroup, c->glist0, c->glist1,
+    void* ptrs[] = {c->rr,    c->slot,  c->ups,   c->stamp,   c->queued, c->lists, c->done, c->qgroup, c->glists,
                     c->ctrl,  c->err_flag, c->log, c->scratch, c->fstage, c->d_mlp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -224,12 +223,11 @@ eik_status eik_create(eik_ctx** out, const int32_t dims[3], double h, const void
         {&c->slot, nb * 2 * kSlot * c->esz},
         {reinterpret_cast<void**>(&c->ups), nb * 2 * 6 * sizeof(unsigned long long)},
         {reinterpret_cast<void**>(&c->stamp), nb * sizeof(unsigned long long)},
-        {reinterpret_cast<void**>(&c->queued), nb * sizeof(int32_t)},
-        {reinterpret_cast<void**>(&c->list0), nb * sizeof(int32_t)},
-        {reinterpret_cast<void**>(&c->list1), nb * sizeof(int32_t)},
-        {reinterpret_cast<void**>(&c->qgroup), static_cast<size_t>(c->ngroups) * sizeof(int32_t)},
-        {reinterpret_cast<void**>(&c->glist0), static_cast<size_t>(c->ngroups) * sizeof(int32_t)},
-        {reinterpret_cast<void**>(&c->glist1), static_cast<size_t>(c->ngroups) * sizeof(int32_t)},
+        {reinterpret_cast<void**>(&c->queued), eikg::kRing * nb * sizeof(int32_t)},
+        {reinterpret_cast<void**>(&c->lists), eikg::kRing * nb * sizeof(int32_t)},
+        {reinterpret_cast<void**>(&c->done), nb * sizeof(int32_t)},
+        {reinterpret_cast<void**>(&c->qgroup), eikg::kRing * static_cast<size_t>(c->ngroups) * sizeof(int32_t)},
+        {reinterpret_cast<void**>(&c->glists), eikg::kRing * static_cast<size_t>(c->ngroups) * sizeof(int32_t)},
         {reinterpret_cast<void**>(&c->ctrl), sizeof(eikg::Ctrl)},
         {reinterpret_cast<void**>(&c->err_flag), sizeof(int)},
     };
@@ -385,14 +383,19 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
     // ---- Alg. 1 for every brick: untouched (psi = +inf) unless it holds fixed nodes
     const size_t nb = static_cast<size_t>(c->nbricks);
     EIK_CK(c, cudaMemsetAsync(c->stamp, 0xFF, nb * sizeof(unsigned long long), s));
-    EIK_CK(c, cudaMemsetAsync(c->queued, 0xFF, nb * sizeof(int32_t), s));
-    if (groups) EIK_CK(c, cudaMemsetAsync(c->qgroup, 0xFF, static_cast<size_t>(c->ngroups) * sizeof(int32_t), s));
+    EIK_CK(c, cudaMemsetAsync(c->queued, 0xFF, eikg::kRing * nb * sizeof(int32_t), s));
+    EIK_CK(c, cudaMemsetAsync(c->lists, 0xFF, eikg::kRing * nb * sizeof(int32_t), s));     // empty entries are -1
+    EIK_CK(c, cudaMemsetAsync(c->done, 0, nb * sizeof(int32_t), s));
+    if (groups) {
+        EIK_CK(c, cudaMemsetAsync(c->qgroup, 0xFF, eikg::kRing * static_cast<size_t>(c->ngroups) * sizeof(int32_t), s));
+        EIK_CK(c, cudaMemsetAsync(c->glists, 0xFF, eikg::kRing * static_cast<size_t>(c->ngroups) * sizeof(int32_t), s));
+    }
     if (nfix > 0)
         EIK_CK(c, eikg::launch_init_sources<T>(nfix, c->d_fix_b, c->d_fix_p, d_fv, static_cast<int>(sb.size()), d_sb,
                                                static_cast<int>(enq.size()), d_enq, static_cast<int>(genq.size()),
-                                               d_genq, static_cast<T*>(c->slot), c->ups, c->stamp, c->queued,
-                                               c->qgroup, static_cast<T*>(c->rr), static_cast<T*>(c->d_saved_r),
-                                               c->list1, c->glist1, s));
+                                               d_genq, static_cast<T*>(c->slot), c->ups, c->stamp, c->queued + nb,
+                                               c->qgroup + c->ngroups, static_cast<T*>(c->rr),
+                                               static_cast<T*>(c->d_saved_r), c->lists + nb, c->glists + c->ngroups, s));
     // ---- control block: restart 1 with bound_1 = 0 + stride
     eikg::Ctrl& H = c->host_ctrl;
     std::memset(&H, 0, sizeof(H));
@@ -405,6 +408,7 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
     H.gcount[1] = static_cast<int32_t>(genq.size());
     H.mode = (P.block_dim == 16) ? 16 : 8;
     H.r_rmin_bits = 0x7f800000u;
+    H.early_now = 1;                          // restart 1 is small (the cells of the sources)
     H.done = enq.empty() ? 1 : 0;
     EIK_CK(c, cudaMemcpyAsync(c->ctrl, &H, sizeof(H), cudaMemcpyHostToDevice, s));
     if (P.log_restarts) {
@@ -430,16 +434,19 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
         L.ups = c->ups;
         L.stamp = c->stamp;
         L.queued = c->queued;
+        L.done = c->done;
+        L.ngroups = c->ngroups;
         L.rr = static_cast<const T*>(c->rr);
-        L.list0 = c->list0;
-        L.list1 = c->list1;
+        for (int r = 0; r < eikg::kRing; ++r) {
+            L.list[r] = c->lists + r * nb;
+            L.glist[r] = c->glists + r * c->ngroups;
+        }
+        L.early = (P.schedule == EIK_SCHED_FIXED && P.block_dim == 8) ? 1 : 0;
         L.GX = c->GX;
         L.GY = c->GY;
         L.GZ = c->GZ;
         L.groups = groups ? 1 : 0;
         L.qgroup = c->qgroup;
-        L.glist0 = c->glist0;
-        L.glist1 = c->glist1;
         L.mode_fixed = (P.block_dim == 16) ? 16 : 8;
         L.ctrl = c->ctrl;
         L.log = P.log_restarts ? c->log : nullptr;
