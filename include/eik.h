@@ -93,10 +93,11 @@ eik_status eik_clear_sources(eik_ctx *ctx);
 /* Schedules of the restart bound (Alg. 6: bound <- min(bound + stride, width)). */
 typedef enum {
     EIK_SCHED_FIXED = 0,   /* every restart advances the bound by `stride` with block edge `block_dim` */
-    EIK_SCHED_LEARNED = 1, /* after each restart the schedule network (eik_set_schedule) picks the stride
-                              and block edge of the next one; `stride` and `block_dim` set restart 1 */
+    EIK_SCHED_LEARNED = 1, /* after restart k the schedule network (eik_set_schedule) picks the stride
+                              and block edge of restart k+2 (one restart ahead, so that waiting warps can
+                              start the next restart early); `stride` and `block_dim` set restarts 1-2 */
     EIK_SCHED_RANDOM = 2   /* each restart's stride and block edge drawn from the action table with
-                              `seed` (to record training data) */
+                              `seed` (to record training data), also one restart ahead */
 } eik_schedule;
 
 typedef struct {
@@ -145,7 +146,8 @@ typedef struct {
     double rmax;            /* max h/F over the marched blocks */
     double ms;              /* device time of the restart */
     int32_t block_dim;      /* block edge of this restart */
-    int32_t next_action;    /* action chosen for the next restart (-1: fixed schedule) */
+    int32_t next_action;    /* action chosen after this restart, for the restart after the next one
+                               (-1: fixed schedule) */
     float features[10];     /* the schedule network's input after this restart */
 } eik_restart_rec;
 

@@ -574,6 +574,7 @@ eik_status batch_queue(eik_batch* b, const std::vector<eik_batch_tile>& tiles, i
     const bool work = !enq.empty() || !genq.empty();
     H.k = work ? 1 : 0;
     H.action = -1;
+    H.pend_action = -1;
     H.count[1] = static_cast<int32_t>(enq.size());
     H.gcount[1] = static_cast<int32_t>(genq.size());
     H.r_rmin_bits = 0x7f800000u;

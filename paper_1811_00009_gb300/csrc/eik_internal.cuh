@@ -76,7 +76,8 @@ struct Ctrl {
     int32_t gcount[kRing];     // group (16^3 block) work-list lengths, by ring slot
     int32_t ghead[kRing];      // next group work-list entry to hand out
     int32_t mode;              // block edge of restart k: 8 (one warp per brick) or 16 (one CTA per group)
-    int32_t action;            // schedule action of restart k (-1: none yet)
+    int32_t action;            // schedule action of restart k (-1: the initial stride and block edge)
+    int32_t pend_action;       // action already chosen for restart k+1 (-1: keep restart k's stride and block edge)
     int32_t early_now;         // restart k's marches publish done[] and waiting warps may start restart k+1
     double bound;              // bound_band of restart k
     double bound_prev;         // bound_band of restart k-1 (-1 at k = 1)

@@ -47,10 +47,27 @@ __device__ inline unsigned mix32(unsigned a) {
     return a;
 }
 
+// Stride and block edge of restart k+1, known from the start of restart k: the
+// schedules choose each restart's action one restart ahead (at the end of
+// restart k-1), so that warps waiting at the barrier of restart k can march
+// restart k+1's bricks early.  -1: restart k's own stride and block edge.
+template <typename T>
+__device__ __forceinline__ void next_restart_of(const LoopParams<T>& P, const Ctrl* C, double* stride, int* mode) {
+    const int pa = __ldcg(&C->pend_action);
+    if (pa >= 0) {
+        *stride = action_stride_h(pa) * P.h;
+        *mode = P.groups ? action_block(pa) : 8;
+    } else {
+        *stride = __ldcg(&C->stride);
+        *mode = __ldcg(&C->mode);
+    }
+}
+
 // Bookkeeping at the end of restart k (run by the warp that reaches the barrier
-// last): statistics, exit test and the next bound of Alg. 6 and, for the
-// learned schedule, the schedule network (one hidden unit per lane) picking
-// the stride and block edge of restart k+1.
+// last): statistics, exit test and the next bound of Alg. 6 (restart k+1 takes
+// the action chosen at the end of restart k-1) and, for the learned schedule,
+// the schedule network (one hidden unit per lane) choosing the stride and
+// block edge of restart k+2 from the front after restart k.
 template <typename T>
 __device__ void restart_end(const LoopParams<T>& P, int lane) {
     static_assert(kHid == 32, "one hidden unit per lane");
@@ -89,25 +106,23 @@ __device__ void restart_end(const LoopParams<T>& P, int lane) {
         __syncwarp();
     }
     if (lane != 0) return;
-    // the next restart's stride and block edge
-    double next_stride = __ldcg(&C->stride);
-    int next_mode = P.mode_fixed;
+    // restart k+1: the action chosen one restart ago
+    double next_stride;
+    int next_mode;
+    next_restart_of(P, C, &next_stride, &next_mode);
+    const int next_action = __ldcg(&C->pend_action);
+    // restart k+2: chosen now (-1: keep the stride and block edge)
     int action = -1;
     if (P.sched == 1 && P.mlp != nullptr) {
         action = 0;
         for (int a = 1; a < kAct; ++a)
             if (s_y[a] < s_y[action]) action = a;           // lowest predicted cost rate
-        const int cur = __ldcg(&C->action);
+        const int cur = next_action >= 0 ? next_action : __ldcg(&C->action);
         if (cur >= 0 && s_y[cur] - s_y[action] <= P.margin) action = cur;   // not worth a switch
-        if (!(s_y[action] == s_y[action])) action = -1;    // network output unusable: keep the fixed stride
+        if (!(s_y[action] == s_y[action])) action = -1;    // network output unusable: keep the stride
     } else if (P.sched == 2) {
         action = static_cast<int>(mix32(P.seed * 0x9e3779b9u + static_cast<unsigned>(k)) % kAct);
     }
-    if (action >= 0) {
-        next_stride = action_stride_h(action) * P.h;
-        next_mode = action_block(action);
-    }
-    if (!P.groups) next_mode = 8;
     const int n_next = (next_mode == 16) ? __ldcg(&C->gcount[s1]) : __ldcg(&C->count[s1]);
     const unsigned long long now = globaltimer();
     const unsigned long long acc_a = __ldcg(&C->r_accepted), acc_band = __ldcg(&C->r_band);
@@ -160,7 +175,8 @@ __device__ void restart_end(const LoopParams<T>& P, int lane) {
         C->k = k + 1;
         C->early_now = (P.early && n_next < kEarlyPerWarp * static_cast<int>(gridDim.x) * kWarps) ? 1 : 0;
         C->mode = next_mode;
-        C->action = action;
+        C->action = next_action;
+        C->pend_action = action;
         C->stride = next_stride;
         C->bound_prev = bnd;
         C->bound = bnd + next_stride;               // bound_band <- bound_band + stride (width = +inf)
@@ -194,8 +210,11 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P
         if (lane == 0) {
             L.bound = __ldcg(&C->bound);
             L.bprev = __ldcg(&C->bound_prev);
-            L.next_bound = L.bound + __ldcg(&C->stride);      // restart k+1's bound under a fixed stride
-            L.early = (P.early && __ldcg(&C->early_now) && mode == 8) ? 1 : 0;
+            double ns;
+            int nm;
+            next_restart_of(P, C, &ns, &nm);
+            L.next_bound = L.bound + ns;                       // restart k+1's bound
+            L.early = (P.early && __ldcg(&C->early_now) && mode == 8 && nm == 8) ? 1 : 0;
             L.n = (mode == 8) ? __ldcg(&C->count[s]) : 0;
             L.waiting = 0;
             L.polls = 0;

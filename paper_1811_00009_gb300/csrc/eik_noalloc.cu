@@ -272,6 +272,7 @@ eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float* F, in
     H.count[1] = nenq;
     H.mode = 8;
     H.action = -1;
+    H.pend_action = -1;
     H.r_rmin_bits = 0x7f800000u;
     H.early_now = 1;                          // restart 1 is small (the cells of the sources)
     H.done = nenq ? 0 : 1;

@@ -401,6 +401,7 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
     std::memset(&H, 0, sizeof(H));
     H.k = enq.empty() ? 0 : 1;
     H.action = -1;
+    H.pend_action = -1;
     H.bound_prev = -1.0;
     H.stride = P.stride;
     H.bound = 0.0 + P.stride;
@@ -441,7 +442,7 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
             L.list[r] = c->lists + r * nb;
             L.glist[r] = c->glists + r * c->ngroups;
         }
-        L.early = (P.schedule == EIK_SCHED_FIXED && P.block_dim == 8) ? 1 : 0;
+        L.early = 1;
         L.GX = c->GX;
         L.GY = c->GY;
         L.GZ = c->GZ;

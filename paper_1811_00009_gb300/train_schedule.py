@@ -4,8 +4,9 @@ Data: solves of seeded synthetic grids of the three speed families (seeds
 distinct from the evaluation workloads), each run with every fixed action of
 the table (stride x block edge) and with the seeded random schedule, recording
 per-restart logs (features after restart k, device time of each restart).
-Sample for restart k: input = features after k, action = the one used for
-restart k+1, target = log of the cost rate of the next `horizon` restarts
+Sample for restart k: input = features after k, action = the one chosen then
+(it runs in restart k+2), target = log of the cost rate of the `horizon`
+restarts from k+2
 (device ms per unit h of bound advance).  Training runs on the GPU with the
 library's own kernels (eik_mlp_grad / eik_mlp_adam), full batch, Adam.
 
@@ -75,8 +76,9 @@ def dataset(runs, horizon=2, fixed_only=False):
             continue
         recs, h = run["recs"], run["h"]
         for i in range(len(recs) - 1):
+            # the action chosen after restart i runs in restart i+2 (one restart ahead)
             a = run["fixed"] if run["fixed"] >= 0 else recs[i]["next_action"]
-            nxt = recs[i + 1:i + 1 + horizon]
+            nxt = recs[i + 2:i + 2 + horizon]
             ms = sum(r["ms"] for r in nxt)
             adv = sum(r["stride"] for r in nxt) / h
             if ms <= 0 or not (adv > 0) or not math.isfinite(adv):

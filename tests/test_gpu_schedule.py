@@ -59,9 +59,14 @@ def test_random_schedule_follows_its_actions_and_keeps_psi(eik, orc):
     assert len(log) == st["restarts"]
     modes = {r["block_dim"] for r in log}
     assert modes <= {8, 16} and len(modes) == 2
-    for a, b in zip(log[:-1], log[1:]):
+    # restarts 1 and 2 take the initial stride and block edge; the action chosen
+    # after restart k applies to restart k+2 (chosen one restart ahead)
+    assert log[0]["stride"] == 2 * w.h and log[1]["stride"] == 2 * w.h
+    assert log[0]["block_dim"] == 8 and log[1]["block_dim"] == 8
+    for a, b in zip(log[:-2], log[2:]):
         sh, bd = acts[a["next_action"]]
         assert b["block_dim"] == bd and abs(b["stride"] - sh * w.h) <= 1e-15
+    for a, b in zip(log[:-1], log[1:]):
         assert b["bound"] == a["bound"] + b["stride"]
     fin = np.isfinite(ref)
     assert np.array_equal(np.isfinite(psi), fin)
@@ -95,8 +100,8 @@ def test_learned_schedule_needs_weights(eik):
 
 
 def test_learned_schedule_decides_from_the_network(eik, orc):
-    """With a given network (and no switching margin) the schedule takes, after every restart, the
-    action of lowest output."""
+    """With a given network (and no switching margin) the schedule chooses, after every restart, the
+    action of lowest output (for the restart after the next one)."""
     from oracle import mlp
     w = synth.workload("C3", 80)
     F = synth.round_to(w.speed(), "fp32")
