@@ -33,10 +33,10 @@ if ROOT not in sys.path:
 METRIC = "Eikonal Mpoints/s at 512^3/1024^3 + HBM roofline %; learned vs fixed stride"
 ALGO_BYTES_PER_POINT = {"fp32": 8, "fp64": 16}      # read F once + write psi once
 KERNELS_PER_SOLVE = 4                                # gather_r, init_sources, restart_loop, restore_r
-# DRAM bytes per node of one k_restart_loop launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum for
-# the C4 family at 256^3, fixed stride 2h, 8^3 blocks, FP32), scaled to a full launch by the node count; empty
-# until the current kernel has been captured.
-NCU_TRAFFIC_PER_NODE = {}
+# DRAM bytes of one k_restart_loop launch on the 1024^3 workload (fixed stride 2h, 8^3 blocks, FP32) from a
+# one-pass ncu capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum = 92.55 GB + 52.87 GB),
+# per node; profiles/launches_c4_1024_fixed2h.md gives the command.
+NCU_TRAFFIC_PER_NODE = {"fp32": (92.55e9 + 52.87e9) / 1024 ** 3}
 
 
 def measured_peaks():
@@ -222,10 +222,11 @@ def batch_bench(eik, synth, steps: int, warmup: int, tune_rounds: int, dev):
     finally:
         B.close()
     e8 = sum(1 for t in tiles if t[0] == 8)
-    f = sorted({round(t[1] / (t[0] * r["rmin"]), 4) for t, r in zip(tiles, info)})
+    sh = sorted({round(t[1] / w.h, 3) for t, w in zip(tiles, ws)})
     return {"grids": 64, "points": int(sum(w.npoints for w in ws)), "autotuned": tuned,
             "default_8_2h": default, "tuned_over_default_ms": tuned["ms_per_batch"] / default["ms_per_batch"],
-            "tiles": {"ctas_per_sm": ctas, "blocks_8": e8, "blocks_16": 64 - e8, "stride_factor": f,
+            "tiles": {"ctas_per_sm": ctas, "blocks_8": e8, "blocks_16": 64 - e8,
+                      "stride_h": sh if len(sh) <= 4 else [sh[0], sh[-1]],
                       "tune_seconds": tune_s, "tune_best_ms": tune_ms},
             "latency": "per grid: device time from the start of the launch to the end of its last restart"}
 
@@ -357,9 +358,13 @@ def run_ours(args):
     loop_avg_ms = sum(loop_ms) / len(loop_ms)
     achieved = algo_bytes / (loop_avg_ms * 1e-3) / 1e9
     traffic = NCU_TRAFFIC_PER_NODE.get(prec)
+    traffic_b = traffic * w.npoints if traffic else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic * w.npoints if traffic else None,
-            "traffic_source": "ncu capture at 256^3 (fixed 2h) scaled by the node count" if traffic else None,
+            "traffic": traffic_b,
+            "traffic_source": ("ncu one-pass DRAM capture of a full 1024^3 launch (fixed 2h), per node x nodes"
+                               if traffic else None),
+            "dram_gbs": traffic_b / (loop_avg_ms * 1e-3) / 1e9 if traffic_b else None,
+            "dram_frac": traffic_b / (loop_avg_ms * 1e-3) / 1e9 / peak if traffic_b else None,
             "kernel": "k_restart_loop", "peak_kind": peak_kind,
             "algo_bytes_per_launch": algo_bytes, "launch_ms": loop_avg_ms}
 

@@ -329,10 +329,11 @@ eik_status eik_batch_result(eik_batch *b, int32_t i, void *psi_out, int out_on_d
 
 /*
  * eik_batch_autotune -- pick the tiles and CTAs per SM of this batch by timing
- * it on the device (each run is a full eik_batch_solve).  Candidates: stride
- * factor f in {0.5, 0.75, 1, 1.5, 2} (stride of grid s = f * edge_s * rmin_s,
- * rmin_s = min h/F), block edge 16 for the grids with at least m bricks,
- * m in {never, 2048, 512, 0}, and every CTAs-per-SM count that fits.  Search:
+ * it on the device (each run is a full eik_batch_solve).  Candidates: stride of
+ * grid s = c * h_s with c in {1.5, 2, 2.5, 3, 4}, or f * edge_s * rmin_s with
+ * f in {0.5, 0.75, 1, 1.5, 2} (rmin_s = min h/F), block edge 16 for the grids
+ * with at least m bricks, m in {never, 2048, 512, 0}, and every CTAs-per-SM
+ * count that fits.  Search:
  * successive halving -- time every candidate once, keep the best third, time
  * the survivors twice as often, and so on until one is left (at most `rounds`
  * rounds; 0 = no limit).  The winner is kept in the batch for later solves

@@ -699,12 +699,14 @@ eik_status batch_run_timed(eik_batch* b, const std::vector<eik_batch_tile>& tile
     return EIK_OK;
 }
 
-// Candidate table of the autotuner.  Stride of grid s: factor * edge * rmin_s,
-// rmin_s = min h/F over the grid (the time a front at the largest speed takes
-// to cross one block is edge * rmin_s; a larger stride lets the bound outrun
-// what one exchange per restart can carry); block edge 16 for the grids with
-// at least `min16` bricks; launch with ctas CTAs per SM.
+// Candidate table of the autotuner.  Stride of grid s: factor * h_s (per_h),
+// or factor * edge * rmin_s with rmin_s = min h/F over the grid (the time a
+// front at the largest speed takes to cross one block is edge * rmin_s; a
+// larger stride lets the bound outrun what one exchange per restart carries);
+// block edge 16 for the grids with at least `min16` bricks; launch with ctas
+// CTAs per SM.
 struct Cand {
+    bool per_h;
     double factor;
     int64_t min16;
     int ctas;
@@ -716,7 +718,7 @@ std::vector<eik_batch_tile> tiles_of(const eik_batch* b, const Cand& c) {
         const BGrid& G = b->g[i];
         const int e = (G.nb >= c.min16) ? 16 : 8;
         const double r = (std::isfinite(G.rmin) && G.rmin > 0.0) ? G.rmin : G.h;
-        t[i] = eik_batch_tile{e, c.factor * e * r};
+        t[i] = eik_batch_tile{e, c.per_h ? c.factor * G.h : c.factor * e * r};
     }
     return t;
 }
@@ -724,11 +726,14 @@ std::vector<eik_batch_tile> tiles_of(const eik_batch* b, const Cand& c) {
 template <typename T>
 eik_status autotune(eik_batch* b, int32_t rounds_cap, eik_batch_tile* tiles_out, int32_t* ctas_out, double* ms_out) {
     const double factors[] = {0.5, 0.75, 1.0, 1.5, 2.0};
+    const double per_h[] = {1.5, 2.0, 2.5, 3.0, 4.0};
     const int64_t min16s[] = {INT64_MAX, 2048, 512, 0};
     std::vector<Cand> cands;
-    for (double f : factors)
-        for (int64_t m : min16s)
-            for (int c = 1; c <= b->per_sm_max; ++c) cands.push_back(Cand{f, m, c});
+    for (int c = b->per_sm_max; c >= 1; --c)                 // the default tiles (8^3, 2h, all CTAs) first
+        for (int64_t m : min16s) {
+            for (double f : per_h) cands.push_back(Cand{true, f, m, c});
+            for (double f : factors) cands.push_back(Cand{false, f, m, c});
+        }
     eik_batch_params P;
     default_batch_params(&P);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
