@@ -76,7 +76,6 @@ __device__ void batch_restart_end(const LoopParams<T>& P) {
         C->t_end = now;
     } else {
         C->k = k + 1;
-        C->early_now = (P.early && n_next < kEarlyPerWarp * static_cast<int>(gridDim.x) * kWarps) ? 1 : 0;
         C->t_restart = now;
     }
 }
@@ -93,21 +92,23 @@ template <typename T>
 __global__ void __launch_bounds__(kWarps * 32, 3) k_batch_loop(LoopParams<T> P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
+    __shared__ LoopState s_state[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<T>* SW = reinterpret_cast<WarpSmem<T>*>(smem_raw);
+    LoopState& L = s_state[warp];              // the loop's bookkeeping, kept out of registers
     Ctrl* C = P.ctrl;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const unsigned long long t0 = globaltimer();
         C->t_begin = t0;
         C->t_restart = t0;
     }
+    if (lane == 0) L.claim = -1;
     MarchAcc acc{0u, 0u, 0, 0u, 0u, 0u, __int_as_float(0x7f800000), 0.0f};
     bool any = false;
-    int claim = -1;                            // brick-list entry of the next restart claimed while waiting
     for (;;) {
         const int k = __ldcg(&C->k);
         const int s = k % kRing;
-        const bool early_k = P.early && __ldcg(&C->early_now);
+        const bool early_k = P.early != 0;
         if (P.early) clear_used_slot(P, k);
         // ---- 16^3 blocks: one CTA per group of 2x2x2 bricks
         {
@@ -148,42 +149,54 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_batch_loop(LoopParams<T> P) 
         // ---- 8^3 blocks, one warp per brick: this restart's list, then -- once
         // arrived at the barrier -- restart k+1's bricks whose neighbourhood has
         // finished restart k.  One march call site for both.
-        const int n = __ldcg(&C->count[s]);
-        bool waiting = false;
-        unsigned gen = 0;
-        int polls = 0;
-        unsigned nap = 256;
+        if (lane == 0) {
+            L.n = __ldcg(&C->count[s]);
+            L.waiting = 0;
+            L.polls = 0;
+            L.nap = 256;
+        }
+        __syncwarp();
         for (;;) {
             int32_t b = -1;
             int kk = k;
-            if (!waiting) {
+            if (!L.waiting) {
                 int i = -1;
                 if (lane == 0) {
-                    if (claim >= 0 && claim < n) i = claim;    // claimed before the entry existed
+                    const int n = L.n;
+                    if (L.claim >= 0 && L.claim < n) i = L.claim;    // claimed before the entry existed
                     else {
                         const int j = atomicAdd(&C->head[s], 1);
                         if (j < n) i = j;
                     }
+                    L.claim = -1;
                 }
                 i = __shfl_sync(kFull, i, 0);
-                claim = -1;
                 if (i >= 0) b = take_entry(P.list[s], i, false, 0, lane);
                 if (b < 0) {
                     if (any) flush_acc(C, acc, lane);
                     any = false;
+                    unsigned gen;
                     if (barrier_arrive(C, lane, &gen)) {
                         if (lane == 0) batch_restart_end<T>(P);
                         barrier_release(C, lane, gen);
                         break;
                     }
-                    waiting = true;
+                    if (lane == 0) {
+                        L.gen = gen;
+                        L.waiting = 1;
+                    }
+                    __syncwarp();
                     continue;
                 }
             } else {
-                const int st = barrier_poll(C, lane, gen);
+                const int st = barrier_poll(C, lane, L.gen);
                 if (st == 2) return;
                 if (st == 1) break;
-                if (early_k) b = early_entry(C, P.list[(k + 1) % kRing], (k + 1) % kRing, claim, P.wait_limit, lane);
+                if (early_k) {
+                    int claim = L.claim;
+                    b = early_entry(C, P.list[(k + 1) % kRing], (k + 1) % kRing, claim, P.wait_limit, lane);
+                    if (lane == 0) L.claim = claim;
+                }
                 if (b >= 0) {
                     const SolveDesc D = P.solves[__ldg(P.bsolve + b)];
                     const Geo G{D.BX, D.BY, D.BZ, D.boff, D.GX, D.GY, D.goff, 1u};
@@ -194,18 +207,25 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_batch_loop(LoopParams<T> P) 
                     return;
                 }
                 if (b < 0) {
-                    if (++polls > P.wait_limit) {
-                        if (lane == 0) atomicOr(&C->status, kStWaitTimeout);
-                        return;
+                    int quit = 0;
+                    unsigned nap = 0;
+                    if (lane == 0) {
+                        quit = ++L.polls > P.wait_limit;
+                        nap = L.nap;
+                        if (L.nap < 4096) L.nap <<= 1;
+                        if (quit) atomicOr(&C->status, kStWaitTimeout);
                     }
-                    __nanosleep(nap);
-                    if (nap < 4096) nap <<= 1;
+                    if (__shfl_sync(kFull, quit, 0)) return;
+                    __nanosleep(__shfl_sync(kFull, nap, 0));
                     continue;
                 }
                 kk = k + 1;
-                polls = 0;
-                nap = 256;
+                if (lane == 0) {
+                    L.polls = 0;
+                    L.nap = 256;
+                }
             }
+            __syncwarp();
             const int sv = __ldg(P.bsolve + b);
             const SolveDesc D = P.solves[sv];
             const Geo G{D.BX, D.BY, D.BZ, D.boff, D.GX, D.GY, D.goff, 1u};
@@ -578,7 +598,6 @@ eik_status batch_queue(eik_batch* b, const std::vector<eik_batch_tile>& tiles, i
     H.count[1] = static_cast<int32_t>(enq.size());
     H.gcount[1] = static_cast<int32_t>(genq.size());
     H.r_rmin_bits = 0x7f800000u;
-    H.early_now = 1;                          // restart 1 is small (the cells of the sources)
     H.done = work ? 0 : 1;
     EIKB_CK(b, cudaMemcpyAsync(b->ctrl, &H, sizeof(H), cudaMemcpyHostToDevice, s));
     if (work) {

@@ -39,7 +39,6 @@ constexpr int kXF0 = 512;          // offset of the x = 0 face inside a copy
 constexpr int kXF7 = 576;          // offset of the x = 7 face
 constexpr int kWarps = 8;          // warps per CTA of the restart loop (one brick per warp)
 constexpr int kRing = 4;           // work lists in flight: restart k's, k+1's, k+2's (early k+1 marches), k-1's (being cleared)
-constexpr int kEarlyPerWarp = 8;   // early work only in restarts with fewer list entries than this per warp
 
 constexpr unsigned long long kUntouched = ~0ull;   // stamp of a brick no march has written
 constexpr unsigned kNever = 0x7fffffffu;           // "other copy never written"
@@ -78,7 +77,6 @@ struct Ctrl {
     int32_t mode;              // block edge of restart k: 8 (one warp per brick) or 16 (one CTA per group)
     int32_t action;            // schedule action of restart k (-1: the initial stride and block edge)
     int32_t pend_action;       // action already chosen for restart k+1 (-1: keep restart k's stride and block edge)
-    int32_t early_now;         // restart k's marches publish done[] and waiting warps may start restart k+1
     double bound;              // bound_band of restart k
     double bound_prev;         // bound_band of restart k-1 (-1 at k = 1)
     double stride;             // stride that produced `bound`
@@ -138,7 +136,6 @@ struct LoopParams {
     int32_t* qgroup;           // kRing x ngroups, as queued
     int32_t* glist[kRing];     // group work lists by ring slot
     int32_t early;             // non-zero: waiting warps may march the next restart's bricks early
-                               // (in restarts with fewer than kEarlyPerWarp list entries per warp)
     Ctrl* ctrl;
     RestartRec* log;
     int64_t log_cap;

@@ -173,7 +173,6 @@ __device__ void restart_end(const LoopParams<T>& P, int lane) {
     } else {
         const double bnd = __ldcg(&C->bound);
         C->k = k + 1;
-        C->early_now = (P.early && n_next < kEarlyPerWarp * static_cast<int>(gridDim.x) * kWarps) ? 1 : 0;
         C->mode = next_mode;
         C->action = next_action;
         C->pend_action = action;
@@ -214,7 +213,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P
             int nm;
             next_restart_of(P, C, &ns, &nm);
             L.next_bound = L.bound + ns;                       // restart k+1's bound
-            L.early = (P.early && __ldcg(&C->early_now) && mode == 8 && nm == 8) ? 1 : 0;
+            L.early = (P.early && mode == 8 && nm == 8) ? 1 : 0;
             L.n = (mode == 8) ? __ldcg(&C->count[s]) : 0;
             L.waiting = 0;
             L.polls = 0;

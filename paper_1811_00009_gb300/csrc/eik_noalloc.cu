@@ -274,7 +274,6 @@ eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float* F, in
     H.action = -1;
     H.pend_action = -1;
     H.r_rmin_bits = 0x7f800000u;
-    H.early_now = 1;                          // restart 1 is small (the cells of the sources)
     H.done = nenq ? 0 : 1;
     // state that must start fresh: stamps and work-list marks (all ones), control block
     NA_CK(cudaMemsetAsync(stampv, 0xFF, static_cast<size_t>(nb) * sizeof(unsigned long long), st));

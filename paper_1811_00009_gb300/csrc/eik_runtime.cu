@@ -409,7 +409,6 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
     H.gcount[1] = static_cast<int32_t>(genq.size());
     H.mode = (P.block_dim == 16) ? 16 : 8;
     H.r_rmin_bits = 0x7f800000u;
-    H.early_now = 1;                          // restart 1 is small (the cells of the sources)
     H.done = enq.empty() ? 1 : 0;
     EIK_CK(c, cudaMemcpyAsync(c->ctrl, &H, sizeof(H), cudaMemcpyHostToDevice, s));
     if (P.log_restarts) {
