@@ -116,6 +116,9 @@ typedef struct {
                                before and right after the restart-loop kernel (NULL: none) */
     double switch_margin;   /* EIK_SCHED_LEARNED: keep the current action unless another one's predicted
                                log cost rate is lower by more than this (default 0.02) */
+    double width;           /* width_band of Alg. 6 (0 = +inf: the full solve).  A finite width caps the
+                               bound: psi is exact at every node with psi <= width; a node above it keeps a
+                               tentative value >= its exact one, or +inf */
 } eik_params;
 
 /* Per-solve statistics, filled by eik_solve / eik_wait. */

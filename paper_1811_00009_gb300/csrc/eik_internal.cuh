@@ -136,6 +136,7 @@ struct LoopParams {
     int32_t* qgroup;           // kRing x ngroups, as queued
     int32_t* glist[kRing];     // group work lists by ring slot
     int32_t early;             // non-zero: waiting warps may march the next restart's bricks early
+    double width;              // width_band of Alg. 6 (+inf: the full solve)
     Ctrl* ctrl;
     RestartRec* log;
     int64_t log_cap;

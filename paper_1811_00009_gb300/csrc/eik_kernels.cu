@@ -178,7 +178,7 @@ __device__ void restart_end(const LoopParams<T>& P, int lane) {
         C->pend_action = action;
         C->stride = next_stride;
         C->bound_prev = bnd;
-        C->bound = bnd + next_stride;               // bound_band <- bound_band + stride (width = +inf)
+        C->bound = fmin(bnd + next_stride, P.width);   // bound_band <- min(bound_band + stride, width_band)
         C->t_restart = now;
     }
 }
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P
             double ns;
             int nm;
             next_restart_of(P, C, &ns, &nm);
-            L.next_bound = L.bound + ns;                       // restart k+1's bound
+            L.next_bound = fmin(L.bound + ns, P.width);         // restart k+1's bound
             L.early = (P.early && mode == 8 && nm == 8) ? 1 : 0;
             L.n = (mode == 8) ? __ldcg(&C->count[s]) : 0;
             L.waiting = 0;

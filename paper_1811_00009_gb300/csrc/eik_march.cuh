@@ -805,7 +805,8 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
         P.stamp[b] = make_stamp(k, st == kUntouched ? static_cast<int>(kNever) : stamp_latest(st), ns);
 
     // ---- activation for restart k+1 (A of Alg. 4/5, C of Alg. 4)
-    if (lane == 6 && n > 0) enqueue_next(P, G, k, b);
+    // (once the bound has reached width_band, pending nodes above it stay tentative: Alg. 6's A flag)
+    if (lane == 6 && n > 0 && bound_d < P.width) enqueue_next(P, G, k, b);
     if (lane < 6 && um[lane] != 0ull && nbr[lane] >= 0) enqueue_next(P, G, k, nbr[lane]);
     if (lane == 0) acc.band += n;
     // publish: the brick's restart-k march has finished (read by early marches

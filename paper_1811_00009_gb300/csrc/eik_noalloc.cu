@@ -153,6 +153,8 @@ eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float* F, in
     if (P.schedule != EIK_SCHED_FIXED) return fail(EIK_ENOTSUP, "eik_solve_noalloc: fixed-stride schedule only");
     if (P.window == 0.0) P.window = 2.0;
     if (!(P.window > 0.0) || !std::isfinite(P.window)) return fail(EIK_EINVAL, "eik_solve_noalloc: bad window");
+    if (P.width == 0.0) P.width = INFINITY;
+    if (!(P.width > 0.0)) return fail(EIK_EINVAL, "eik_solve_noalloc: width must be >= 0 (0 = +inf)");
     if (P.max_restarts <= 0) P.max_restarts = int64_t(1) << 24;
     const int nx = dims[0], ny = dims[1], nz = dims[2];
     const int BX = (nx + 7) / 8, BY = (ny + 7) / 8, BZ = (nz + 7) / 8;
@@ -268,7 +270,7 @@ eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float* F, in
     H.k = nenq ? 1 : 0;
     H.bound_prev = -1.0;
     H.stride = P.stride;
-    H.bound = 0.0 + P.stride;
+    H.bound = std::fmin(0.0 + P.stride, P.width);
     H.count[1] = nenq;
     H.mode = 8;
     H.action = -1;
@@ -317,6 +319,7 @@ eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float* F, in
         L.log = nullptr;
         L.log_cap = 0;
         L.window = P.window;
+        L.width = P.width;
         L.fallback_tau = P.fallback_tau;
         L.max_restarts = P.max_restarts;
         L.wait_limit = (long long)1 << 26;

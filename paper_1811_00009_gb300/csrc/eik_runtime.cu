@@ -404,7 +404,7 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
     H.pend_action = -1;
     H.bound_prev = -1.0;
     H.stride = P.stride;
-    H.bound = 0.0 + P.stride;
+    H.bound = std::fmin(0.0 + P.stride, P.width);
     H.count[1] = static_cast<int32_t>(enq.size());
     H.gcount[1] = static_cast<int32_t>(genq.size());
     H.mode = (P.block_dim == 16) ? 16 : 8;
@@ -454,6 +454,7 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
         L.window = P.window;
         L.fallback_tau = P.fallback_tau;
         L.max_restarts = P.max_restarts;
+        L.width = P.width;
         L.wait_limit = (long long)1 << 26;
         L.sched = P.schedule;
         L.mlp = (P.schedule == EIK_SCHED_LEARNED) ? c->d_mlp : nullptr;
@@ -484,6 +485,7 @@ eik_status check_params(eik_ctx* c, const eik_params* p) {
     if (!(p->fallback_tau >= 0.0) || !(p->fallback_tau <= 1.0))
         return fail(c, EIK_EINVAL, "fallback_tau must lie in [0, 1]");
     if (p->max_restarts < 0) return fail(c, EIK_EINVAL, "max_restarts must be >= 0");
+    if (!(p->width >= 0.0)) return fail(c, EIK_EINVAL, "width must be >= 0 (0 = +inf)");
     return EIK_OK;
 }
 
@@ -501,6 +503,7 @@ eik_status eik_solve_async(eik_ctx* c, const eik_params* params) {
     if (P.block_dim == 0) P.block_dim = 8;
     if (P.max_restarts == 0) P.max_restarts = int64_t(1) << 24;
     if (P.window == 0.0) P.window = 2.0;
+    if (P.width == 0.0) P.width = INFINITY;
     c->params = P;
     st = (c->prec == EIK_FP32) ? queue_solve<float>(c, P) : queue_solve<double>(c, P);
     if (st != EIK_OK) return st;

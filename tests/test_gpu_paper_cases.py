@@ -1,0 +1,68 @@
+"""The paper's own test problems (Sec. 3.1, Cases 1-4) on its cell-centred grid, on the GPU.
+
+Case 4 has F = 0 spherical shells with holes (barrier nodes that are never solved and nodes sealed off
+behind them).  Every case must match the FP64 oracle (FP64: max-rel <= 1e-12 with identical +inf sets;
+FP32: max-abs <= 1e-5 * max psi), for small, paper-optimal and infinite strides and both block edges; and
+the number of restarts must not depend on the block edge while the stride is at most 2h / F_max (Sec. 3.4).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eik():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1811_00009_gb300 import build
+    build.build()
+    import paper_1811_00009_gb300 as E
+    return E
+
+
+def solve(eik, F, h, src, precision, stride, bd):
+    dt = np.float32 if precision == "fp32" else np.float64
+    n = F.shape[0]
+    with eik.Solver((n, n, n), h, np.ascontiguousarray(F.astype(dt)), precision) as S:
+        S.add_sources(src)
+        st = S.solve(stride, block_dim=bd)
+        return S.result().astype(np.float64), st
+
+
+@pytest.mark.parametrize("case", [1, 2, 3, 4])
+def test_paper_case_fp64(eik, orc, case):
+    F, h, src = synth.speed_paper_case(case, 48)
+    ref = orc.fmm(F, h, src)
+    fin = np.isfinite(ref)
+    if case == 4:
+        assert (F == 0).any() and not fin.all()        # barriers and sealed-off nodes exist
+    nr = {}
+    for bd in (8, 16):
+        for s in (0.5, 2.0, math.inf):
+            psi, st = solve(eik, F, h, src, "fp64", s * h, bd)
+            assert np.array_equal(np.isfinite(psi), fin), (case, bd, s)
+            pos = fin & (ref > 0)
+            assert np.max(np.abs(psi[pos] - ref[pos]) / ref[pos]) <= 1e-12, (case, bd, s)
+            nr[(bd, s)] = st["restarts"]
+    fmax = float(F.max())
+    if 0.5 * fmax <= 2.0:
+        assert nr[(8, 0.5)] == nr[(16, 0.5)], nr
+
+
+@pytest.mark.parametrize("case", [1, 2, 3, 4])
+def test_paper_case_fp32(eik, orc, case):
+    F, h, src = synth.speed_paper_case(case, 96)
+    F = synth.round_to(F, "fp32")
+    ref = orc.fmm(F, h, src)
+    fin = np.isfinite(ref)
+    for s in (1.5, 2.0, 3.5):
+        psi, st = solve(eik, F, h, src, "fp32", s * h, 8)
+        assert np.array_equal(np.isfinite(psi), fin), (case, s)
+        assert np.max(np.abs(psi[fin] - ref[fin])) <= 1e-5 * float(ref[fin].max()), (case, s)
+        assert st["fallbacks"] == 0 or case == 3                 # Case 3's F nearly vanishes in places

@@ -84,3 +84,18 @@ def test_infinite_stride_is_the_naive_block_method(orc):
     nr = [orc.block_fmm(F, w.h, w.sources, b, math.inf)[1]["nr"] for b in (48, 24, 12)]
     assert nr[0] == 1
     assert nr[0] < nr[1] < nr[2]
+
+
+def test_finite_width_band_is_exact_below_the_width(orc):
+    """Alg. 6 with a finite width_band: every node with psi <= width gets the full solution's value, and
+    every node above it keeps a tentative value no smaller than its exact one (or +inf)."""
+    w = synth.workload("C3", 40)
+    F = w.speed()
+    full = orc.fmm(F, w.h, w.sources)
+    width = 0.35 * float(full[np.isfinite(full)].max())
+    part, st = orc.block_fmm(F, w.h, w.sources, 8, 2 * w.h, width=width)
+    low = full <= width
+    assert np.max(np.abs(part[low] - full[low]) / np.maximum(full[low], 1e-300)) <= 1e-12
+    high = ~low & np.isfinite(full)
+    assert np.all(part[high] >= full[high] * (1 - 1e-12))
+    assert np.isinf(part).any()
