@@ -4,20 +4,23 @@
 // ghost exchange of Alg. 5).
 //
 // One warp marches one 8x8x8 block (a "brick").  The brick's psi, h/F and its
-// six ghost faces sit in shared memory; lane L owns the two x-rows
-// (y = L & 7, z = 2*(L >> 3) + {0, 1}) as a 16-bit mask, plus the ghost nodes
-// next to them.  The band (Sec. 2.1 BAND set) is a list of halo indices shared
-// by the warp; a band node's value carries its sign bit set in shared memory
-// so that any lane can tell a tentative value from an accepted (KNOWN) one
-// with one load.
+// six ghost faces sit in shared memory; lane L loads and writes back the two
+// x-rows (y = L & 7, z = 2*(L >> 3) + {0, 1}) and face-local nodes 2L, 2L+1 of
+// each ghost face.  The band (Sec. 2.1 BAND set) is a list of halo indices
+// shared by the warp; a band node's value carries its sign bit set in shared
+// memory so that any lane can tell a tentative value from an accepted (KNOWN)
+// one with one load.
 //
-// Ordered extraction (Alg. 4) is done in rounds: each round takes the band
-// minimum m with a warp reduction and accepts every band node with
-// psi <= min(m + w, bound), w = omega * min(h/F) over the brick; the
-// neighbours of the accepted nodes (Alg. 2) are compacted into a list and
+// Ordered extraction (Alg. 4) is done in rounds: each round accepts every band
+// node with psi <= min(m + w, bound), m the band minimum, w = omega * min(h/F)
+// over the brick; the accepted nodes' neighbours (Alg. 2) come from shifting a
+// halo bit vector of the accepted nodes, are compacted into a list and
 // re-solved (Alg. 3) 32 at a time.  A lowered node rejoins the band, so an
 // accepted node can be refreshed later exactly as a KNOWN_NEW node of the
 // paper can.  With w = 0 this is the paper's one-node-at-a-time order.
+//
+// The rest of the file is the restart loop's shared machinery: the work-list
+// ring, the per-warp grid barrier and the early marches of the next restart.
 #pragma once
 
 #include "eik_internal.cuh"
