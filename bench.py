@@ -34,9 +34,9 @@ METRIC = "Eikonal Mpoints/s at 512^3/1024^3 + HBM roofline %; learned vs fixed s
 ALGO_BYTES_PER_POINT = {"fp32": 8, "fp64": 16}      # read F once + write psi once
 KERNELS_PER_SOLVE = 4                                # gather_r, init_sources, restart_loop, restore_r
 # DRAM bytes of one k_restart_loop launch on the 1024^3 workload (fixed stride 2h, 8^3 blocks, FP32) from a
-# one-pass ncu capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum = 92.55 GB + 52.87 GB),
+# one-pass ncu capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum = 93.12 GB + 53.34 GB),
 # per node; profiles/launches_c4_1024_fixed2h.md gives the command.
-NCU_TRAFFIC_PER_NODE = {"fp32": (92.55e9 + 52.87e9) / 1024 ** 3}
+NCU_TRAFFIC_PER_NODE = {"fp32": (93.12e9 + 53.34e9) / 1024 ** 3}
 
 
 def measured_peaks():
