@@ -621,7 +621,7 @@ eik_status batch_queue(eik_batch* b, const std::vector<eik_batch_tile>& tiles, i
         L.fallback_tau = P.fallback_tau;
         L.max_restarts = P.max_restarts;
         L.width = INFINITY;                    // full solves
-        L.wait_limit = (long long)1 << 26;
+        L.wait_limit = eikg::kWaitPolls;
         L.solves = b->d_solves;
         L.bsolve = b->bsolve;
         L.gsolve = b->gsolve;

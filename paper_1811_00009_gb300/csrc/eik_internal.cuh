@@ -38,6 +38,7 @@ constexpr int kSlot = 640;         // values per brick copy
 constexpr int kXF0 = 512;          // offset of the x = 0 face inside a copy
 constexpr int kXF7 = 576;          // offset of the x = 7 face
 constexpr int kWarps = 8;          // warps per CTA of the restart loop (one brick per warp)
+constexpr long long kWaitPolls = 1ll << 22;   // polls (naps of 32 ns to 4 us) before a wait gives up: seconds
 constexpr int kRing = 4;           // work lists in flight: restart k's, k+1's, k+2's (early k+1 marches), k-1's (being cleared)
 
 constexpr unsigned long long kUntouched = ~0ull;   // stamp of a brick no march has written
@@ -143,7 +144,7 @@ struct LoopParams {
     double window;             // omega: acceptance window = omega * min(h/F) over the brick
     double fallback_tau;       // FP32: double-precision root when D < tau * k * r^2
     int64_t max_restarts;
-    long long wait_limit;      // spin iterations before a barrier wait gives up
+    long long wait_limit;      // polls before a wait (barrier, list entry, neighbour march) gives up
     int32_t sched;             // 0 fixed, 1 learned, 2 seeded random (exploration data)
     int32_t mode_fixed;        // block edge of every restart under the fixed schedule (8 or 16)
     const float* mlp;          // schedule network weights (learned schedule)

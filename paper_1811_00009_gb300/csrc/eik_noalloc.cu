@@ -322,7 +322,7 @@ eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float* F, in
         L.width = P.width;
         L.fallback_tau = P.fallback_tau;
         L.max_restarts = P.max_restarts;
-        L.wait_limit = (long long)1 << 26;
+        L.wait_limit = eikg::kWaitPolls;
         L.sched = EIK_SCHED_FIXED;
         L.mlp = nullptr;
         L.h = h;

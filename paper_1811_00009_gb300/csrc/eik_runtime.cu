@@ -455,7 +455,7 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
         L.fallback_tau = P.fallback_tau;
         L.max_restarts = P.max_restarts;
         L.width = P.width;
-        L.wait_limit = (long long)1 << 26;
+        L.wait_limit = eikg::kWaitPolls;
         L.sched = P.schedule;
         L.mlp = (P.schedule == EIK_SCHED_LEARNED) ? c->d_mlp : nullptr;
         L.h = c->h;

@@ -138,7 +138,7 @@ def dataset_curves(runs, delta_h=8.0):
     return np.asarray(X, np.float32), np.asarray(A, np.int32), np.asarray(Y, np.float32)
 
 
-def dataset_rollout(runs):
+def dataset_rollout(runs, relative=False):
     """Every logged state labelled for every action with the time to finish.
 
     For each grid, the fixed-action runs give T_a(b) (device time until the
@@ -170,11 +170,15 @@ def dataset_rollout(runs):
             b0 = rec["bound"]
             if not math.isfinite(b0):
                 continue
-            for a, (b, t, tend) in curves.items():
-                rem = tend - (np.interp(b0, b, t) if len(b) else 0.0)
+            ys = {a: math.log(max(tend - (np.interp(b0, b, t) if len(b) else 0.0), 0.0) + 0.01)
+                  for a, (b, t, tend) in curves.items()}
+            # relative: each action against the mean over actions at this state (the decision only
+            # compares actions, and the level, which depends on the grid's size, is left out)
+            base = float(np.mean(list(ys.values()))) if relative else 0.0
+            for a, y in ys.items():
                 X.append(rec["features"])
                 A.append(a)
-                Y.append(math.log(max(rem, 0.0) + 0.01))
+                Y.append(y - base)
     return np.asarray(X, np.float32), np.asarray(A, np.int32), np.asarray(Y, np.float32)
 
 
@@ -282,8 +286,9 @@ def main():
     ap.add_argument("--runs-out", default=None, help="save the collected per-restart records (JSON)")
     ap.add_argument("--runs-in", default=None, help="train from saved records instead of collecting")
     ap.add_argument("--variants", default=None,
-                    help="comma list N:rollout|curves|fixed|all (rollout: every action labelled with the time "
-                         "its fixed-action run needed to finish from the state's bound; curves: the local cost "
+                    help="comma list N:rollout|rollout_rel|curves|fixed|all (rollout: every action labelled with "
+                         "the time its fixed-action run needed to finish from the state's bound; rollout_rel: the "
+                         "same relative to the mean over actions; curves: the local cost "
                          "rate over N h; fixed/all: the taken action over the next N restarts); trains and "
                          "evaluates each, keeps the fastest")
     args = ap.parse_args()
@@ -317,6 +322,8 @@ def main():
             X, A, Y = dataset_curves(runs, delta_h=float(hz))
         elif fo == "rollout":
             X, A, Y = dataset_rollout(runs)
+        elif fo == "rollout_rel":
+            X, A, Y = dataset_rollout(runs, relative=True)
         else:
             X, A, Y = dataset(runs, horizon=hz, fixed_only=(fo == "fixed"))
         print(f"variant {hz} {fo}: {len(Y)} samples", flush=True)
@@ -338,6 +345,7 @@ def main():
                          "log1p(solves)/20"],
             "target": {"rollout": "log(device ms to finish the solve from the state's bound with the action, from "
                                   "the fixed-action runs) + 0.01 ms",
+                       "rollout_rel": "the rollout target minus its mean over the actions at the same state",
                        "curves": f"log(device ms per h of bound advance over the next {hz} h, every action)"}.get(
                            fo, f"log(device ms per h of bound advance over the next {hz} restarts, taken action)")}
     if ev is not None:
