@@ -107,6 +107,33 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def rank_workload(n: int, rank: int):
+    """The 1024^3-family workload of one rank: every rank solves its own instance (its own random field),
+    so ranks share no data and need no collective on the data path (weak scaling)."""
+    import synth
+    w = synth.workload("C4", n)
+    if rank:
+        w.seed += 1000 * rank
+    return w
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest value of x over the ranks (the job is as slow as its slowest rank); x itself when the
+    process group is absent or has one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(points_per_rank: int, steps: int, ranks: int, seconds: float) -> float:
+    """Whole-job throughput in Mpoints/s: the points every rank solved over the slowest rank's time."""
+    return points_per_rank * steps * ranks / seconds / 1e6
+
+
 def setup_dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -289,9 +316,7 @@ def run_ours(args):
     import synth
 
     n = args.n
-    w = synth.workload("C4", n)
-    if rank:
-        w.seed += 1000 * rank                           # independent instance per rank
+    w = rank_workload(n, rank)                          # independent instance per rank
     prec = args.precision
     Fd = w.speed_torch(dev)
     if prec == "fp64":
@@ -329,14 +354,9 @@ def run_ours(args):
         torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
-    elapsed_ms = t_start.elapsed_time(t_end)
+    elapsed_ms = max_over_ranks(t_start.elapsed_time(t_end), dev)
     loop_ms = [a.elapsed_time(b) for a, b in pairs]
-    if ws > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    total_points = w.npoints * args.steps * ws
-    value = total_points / (elapsed_ms * 1e-3) / 1e6
+    value = job_rate(w.npoints, args.steps, ws, elapsed_ms * 1e-3)
 
     # the same workload with the fixed stride (the method without the schedule network)
     sched_cmp = None
@@ -385,13 +405,9 @@ def run_ours(args):
             eik.eik_solve_ex(ctx, stride, **kw)
             eik.eik_result(ctx, out_h.numpy())
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
         nb = Fd.element_size() * w.npoints
-        e2e = {"value": w.npoints * args.e2e_steps * ws / e2e_s / 1e6, "unit": "Mpoints/s",
+        e2e = {"value": job_rate(w.npoints, args.e2e_steps, ws, e2e_s), "unit": "Mpoints/s",
                "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb, "steps": args.e2e_steps}
 
     # accuracy of this run's path against the FP64 oracle on the CPU-baseline sample
