@@ -266,13 +266,18 @@ def evaluate(eik, weights, n=512, reps=3, log=print, cfg="C3"):
     return res
 
 
-def evaluate_all(eik, weights, log=print):
-    """Held-out 512^3 workloads of the three families (their seeds are not in the training grids)."""
+def evaluate_all(eik, weights, log=print, big=False):
+    """Held-out 512^3 workloads of the three families (their seeds are not in the training grids) and,
+    with big, the 1024^3 GRF workload."""
     out = {}
-    for cfg in ("C3", "C4", "C2"):
+    keys = ["C3", "C4", "C2"]
+    for cfg in keys:
         out[cfg] = evaluate(eik, weights, cfg=cfg, log=log)
-    out["mean_learned_over_best_fixed"] = float(np.mean([out[c]["learned_over_best_fixed"] for c in ("C3", "C4", "C2")]))
-    out["mean_learned_over_2h"] = float(np.mean([out[c]["learned_over_2h"] for c in ("C3", "C4", "C2")]))
+    if big:
+        out["C4_1024"] = evaluate(eik, weights, n=1024, reps=2, cfg="C4", log=log)
+        keys.append("C4_1024")
+    out["mean_learned_over_best_fixed"] = float(np.mean([out[c]["learned_over_best_fixed"] for c in keys]))
+    out["mean_learned_over_2h"] = float(np.mean([out[c]["learned_over_2h"] for c in keys]))
     return out
 
 
@@ -282,9 +287,13 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--horizon", type=int, default=8)
     ap.add_argument("--eval", action="store_true")
+    ap.add_argument("--eval-1024", action="store_true", help="also evaluate on the 1024^3 GRF workload")
     ap.add_argument("--quick", action="store_true", help="small data set (tests)")
     ap.add_argument("--runs-out", default=None, help="save the collected per-restart records (JSON)")
-    ap.add_argument("--runs-in", default=None, help="train from saved records instead of collecting")
+    ap.add_argument("--runs-in", default=None,
+                    help="train from saved records instead of collecting (comma-separated files are merged)")
+    ap.add_argument("--collect-grids", default=None,
+                    help="collect these grids (family:edge:seed, comma-separated) and add them to --runs-in")
     ap.add_argument("--variants", default=None,
                     help="comma list N:rollout|rollout_rel|curves|fixed|all (rollout: every action labelled with "
                          "the time its fixed-action run needed to finish from the state's bound; rollout_rel: the "
@@ -305,13 +314,19 @@ def main():
                  for j, n in enumerate((192, 256, 320, 384, 448, 512)) for r in range(2)]
     t0 = time.time()
     if args.runs_in:
-        with open(args.runs_in) as fh:
-            runs = json.load(fh)
+        runs = []
+        for path in args.runs_in.split(","):
+            with open(path) as fh:
+                runs += json.load(fh)
+        if args.collect_grids:
+            extra = [(f, int(n), int(sd)) for f, n, sd in (g.split(":") for g in args.collect_grids.split(","))]
+            runs += collect(eik, extra, actions)
+            grids = grids + extra
     else:
         runs = collect(eik, grids, actions)
-        if args.runs_out:
-            with open(args.runs_out, "w") as fh:
-                json.dump(runs, fh)
+    if args.runs_out:
+        with open(args.runs_out, "w") as fh:
+            json.dump(runs, fh)
     print(f"{len(runs)} runs in {time.time() - t0:.1f} s", flush=True)
     variants = [(0, "rollout")]
     if args.variants:
@@ -328,10 +343,11 @@ def main():
             X, A, Y = dataset(runs, horizon=hz, fixed_only=(fo == "fixed"))
         print(f"variant {hz} {fo}: {len(Y)} samples", flush=True)
         w, hist = train(eik, X, A, Y, steps=args.steps)
-        ev = evaluate_all(eik, w) if (args.eval or args.variants) else None
+        ev = evaluate_all(eik, w, big=args.eval_1024) if (args.eval or args.variants) else None
         if ev is not None:
             print(json.dumps({"horizon": hz, "labels": fo, "C3": ev["C3"]["learned_over_best_fixed"],
                               "C4": ev["C4"]["learned_over_best_fixed"], "C2": ev["C2"]["learned_over_best_fixed"],
+                              "C4_1024": ev.get("C4_1024", {}).get("learned_over_best_fixed"),
                               "mean_vs_best": ev["mean_learned_over_best_fixed"],
                               "mean_vs_2h": ev["mean_learned_over_2h"]}), flush=True)
         score = ev["mean_learned_over_best_fixed"] if ev else 0.0
