@@ -240,11 +240,20 @@ __device__ __forceinline__ void load2_cg<double>(const double* g, double& a, dou
     b = v.y;
 }
 
-template <typename T>
-__device__ __forceinline__ T warp_min(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = vmin(v, __shfl_xor_sync(kFull, v, o));
-    return v;
+// Minimum over the warp of values that are >= 0 (+inf allowed): the bits of
+// non-negative IEEE numbers order like unsigned integers, so one integer
+// reduction (two for FP64: high words, then low words among the lanes holding
+// the smallest high word) replaces the five shuffle-and-min steps.  A NaN sits
+// above +inf as an integer and loses to any number, as it does in fmin.
+__device__ __forceinline__ float warp_min_nn(float v) {
+    return __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(v)));
+}
+__device__ __forceinline__ double warp_min_nn(double v) {
+    const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(v));
+    const unsigned hi = static_cast<unsigned>(u >> 32), lo = static_cast<unsigned>(u);
+    const unsigned mh = __reduce_min_sync(kFull, hi);
+    const unsigned ml = __reduce_min_sync(kFull, hi == mh ? lo : 0xffffffffu);
+    return __longlong_as_double(static_cast<long long>((static_cast<unsigned long long>(mh) << 32) | ml));
 }
 template <typename T>
 __device__ __forceinline__ T warp_max(T v) {
@@ -485,7 +494,7 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
         if (FXOB >> 8) atomicOr(&S.fxob[(pbase + 64) >> 5], (FXOB >> 8) << ((pbase + 64) & 31));
     }
 
-    const T rmin_b = warp_min(rlo);
+    const T rmin_b = warp_min_nn(rlo);
     if (present) {
         acc.rmin = fminf(acc.rmin, static_cast<float>(rmin_b));
         acc.rmax = fmaxf(acc.rmax, static_cast<float>(warp_max(rhi)));
@@ -594,7 +603,7 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
         for (;;) {
             T lmin = INF;
             for (int i = lane; i < n; i += 32) lmin = vmin(lmin, vabs(S.psi[S.band[i]]));
-            T mn = warp_min(lmin);
+            T mn = warp_min_nn(lmin);
             if (lane == 0) s_wmin[warp] = static_cast<double>(mn);
             __syncthreads();
             double g = s_wmin[0];
@@ -699,7 +708,7 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
         __syncwarp();
         T lmin = INF;
         for (int i = lane; i < n; i += 32) lmin = vmin(lmin, vabs(S.psi[S.band[i]]));
-        T mn = warp_min(lmin);
+        T mn = warp_min_nn(lmin);
         for (;;) {
             if (!(mn < INF) || !(mn <= bound)) break;   // band empty, or its minimum above the bound
             if (++rounds > kRoundCap) {
@@ -761,7 +770,7 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
             const int total = compact(d, 32 * lane);
             acc.solves += total;
             const T smin = solve_list(total);
-            mn = warp_min(vmin(kmin, smin));
+            mn = warp_min_nn(vmin(kmin, smin));
         }
     }
     acc.rounds += rounds;
