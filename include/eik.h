@@ -77,6 +77,17 @@ eik_status eik_create(eik_ctx **out, const int32_t dims[3], double h, const void
 eik_status eik_set_speed(eik_ctx *ctx, const void *F, int F_on_device);
 
 /*
+ * eik_set_speed_async -- eik_set_speed without waiting: the copy of F and its
+ * re-layout are queued on the context's stream and the call returns.  F must
+ * stay valid (and unchanged) until eik_sync or the next solve on ctx; host F
+ * should be pinned, or the copy is not asynchronous.  The validation of F is
+ * reported by the next eik_solve_async / eik_solve_ex / eik_solve (which then
+ * do not run) or eik_sync, as EIK_EINVAL.  A later eik_set_speed(_async)
+ * supersedes it.  Errors here: EIK_EINVAL (NULL F), EIK_ESTATE (solve in flight).
+ */
+eik_status eik_set_speed_async(eik_ctx *ctx, const void *F, int F_on_device);
+
+/*
  * eik_add_sources -- add point sources (Gamma of Eq. (1.1)).
  *   xyz  n*3 physical coordinates (x, y, z), origin at node 0, each within
  *        [0, (n_axis - 1)*h].  The nodes of the grid cell containing a source
@@ -187,6 +198,25 @@ eik_status eik_restart_log(eik_ctx *ctx, eik_restart_rec *out, int64_t cap, int6
  * Errors: EIK_ESTATE before the first successful solve.
  */
 eik_status eik_result(eik_ctx *ctx, void *psi_out, int out_on_device);
+
+/*
+ * eik_result_async -- eik_result without waiting for the copy: psi is put in
+ * grid order on the device (the call waits for that kernel, a few ms at
+ * 1024^3, so that a solve queued next on another context's stream starts
+ * after it) and, for a host psi_out, the copy to it is queued on the context's
+ * stream.  psi_out holds the result after eik_sync(ctx) or any later blocking
+ * call on ctx; host psi_out should be pinned.  Two contexts used in turn
+ * overlap one's host copies with the other's solve.  Errors as eik_result.
+ */
+eik_status eik_result_async(eik_ctx *ctx, void *psi_out, int out_on_device);
+
+/*
+ * eik_sync -- wait for everything queued on the context's stream (speed
+ * uploads, result copies, a solve in flight; that solve's statistics still
+ * come from eik_wait).  Returns EIK_EINVAL if an eik_set_speed_async found a
+ * bad F.
+ */
+eik_status eik_sync(eik_ctx *ctx);
 
 /* eik_destroy -- free the context and everything it allocated (NULL is a no-op). */
 void eik_destroy(eik_ctx *ctx);

@@ -105,6 +105,12 @@ def lib():
             L.eik_create.argtypes = [C.POINTER(vp), C.POINTER(i32), dbl, vp, C.c_int, C.c_int, vp]
             L.eik_set_speed.restype = i32
             L.eik_set_speed.argtypes = [vp, vp, C.c_int]
+            L.eik_set_speed_async.restype = i32
+            L.eik_set_speed_async.argtypes = [vp, vp, C.c_int]
+            L.eik_result_async.restype = i32
+            L.eik_result_async.argtypes = [vp, vp, C.c_int]
+            L.eik_sync.restype = i32
+            L.eik_sync.argtypes = [vp]
             L.eik_add_sources.restype = i32
             L.eik_add_sources.argtypes = [vp, i32, C.POINTER(dbl)]
             L.eik_clear_sources.restype = i32
@@ -239,6 +245,14 @@ def eik_set_speed(ctx, F, precision="fp32") -> None:
     _check(lib().eik_set_speed(ctx, ptr, on_dev), ctx)
 
 
+def eik_set_speed_async(ctx, F, precision="fp32"):
+    """Queue the upload of a new speed function; returns F, which must stay alive and unchanged until
+    eik_sync(ctx) or the next solve on ctx (host F should be pinned)."""
+    ptr, on_dev, keep = _buffer(F, np.float32 if _precision(precision) == EIK_FP32 else np.float64)
+    _check(lib().eik_set_speed_async(ctx, ptr, on_dev), ctx)
+    return keep
+
+
 def eik_add_sources(ctx, xyz) -> None:
     a = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
     _check(lib().eik_add_sources(ctx, len(a), a.ctypes.data_as(C.POINTER(C.c_double))), ctx)
@@ -369,6 +383,24 @@ def eik_result(ctx, out):
         raise ValueError("out must be a contiguous float32/float64 tensor or array")
     _check(lib().eik_result(ctx, ptr, on_dev), ctx)
     return out
+
+
+def eik_result_async(ctx, out):
+    """Queue psi into `out` (as eik_result); complete after eik_sync(ctx).  Host `out` should be pinned."""
+    for dt in (np.float32, np.float64):
+        try:
+            ptr, on_dev, keep = _buffer(out, dt)
+            break
+        except ValueError:
+            continue
+    else:
+        raise ValueError("out must be a contiguous float32/float64 tensor or array")
+    _check(lib().eik_result_async(ctx, ptr, on_dev), ctx)
+    return out
+
+
+def eik_sync(ctx) -> None:
+    _check(lib().eik_sync(ctx), ctx)
 
 
 def eik_destroy(ctx) -> None:

@@ -77,6 +77,7 @@ struct eik_ctx {
     std::vector<double> src;
     bool solved = false;
     bool in_flight = false;
+    bool speed_unchecked = false;  // an eik_set_speed_async whose validation flag is not read yet
     int64_t last_nr = 0;
     int loop_grid = 0;
     int sms = 0;
@@ -117,18 +118,25 @@ void free_all(eik_ctx* c) {
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
-// F (x fastest, caller memory) -> h/F in brick layout, with validation.
-eik_status upload_speed(eik_ctx* c, const void* F, int F_on_device) {
+// The device staging buffer for host uploads and host results, grown to `bytes`.
+eik_status ensure_stage(eik_ctx* c, size_t bytes) {
+    if (bytes <= c->fstage_cap) return EIK_OK;
+    if (c->fstage) cudaFree(c->fstage);
+    c->fstage = nullptr;
+    c->fstage_cap = 0;
+    EIK_CK(c, cudaMalloc(&c->fstage, bytes));
+    c->fstage_cap = bytes;
+    return EIK_OK;
+}
+
+// F (x fastest, caller memory) -> h/F in brick layout, with validation (checked
+// here, or left for check_speed when `wait` is false).
+eik_status upload_speed(eik_ctx* c, const void* F, int F_on_device, bool wait = true) {
     const size_t bytes = static_cast<size_t>(c->nx) * c->ny * c->nz * c->esz;
     const void* Fd = F;
     if (!F_on_device) {
-        if (bytes > c->fstage_cap) {
-            if (c->fstage) cudaFree(c->fstage);
-            c->fstage = nullptr;
-            c->fstage_cap = 0;
-            EIK_CK(c, cudaMalloc(&c->fstage, bytes));
-            c->fstage_cap = bytes;
-        }
+        const eik_status st = ensure_stage(c, bytes);
+        if (st != EIK_OK) return st;
         EIK_CK(c, cudaMemcpyAsync(c->fstage, F, bytes, cudaMemcpyHostToDevice, c->stream));
         Fd = c->fstage;
     }
@@ -141,12 +149,41 @@ eik_status upload_speed(eik_ctx* c, const void* F, int F_on_device) {
         EIK_CK(c, eikg::launch_layout_speed<double>(static_cast<const double*>(Fd), static_cast<double*>(c->rr),
                                                     c->nx, c->ny, c->nz, c->BX, c->BY, c->nbricks, c->h,
                                                     c->err_flag, c->stream));
+    if (!wait) {
+        c->speed_unchecked = true;
+        return EIK_OK;
+    }
     int bad = 0;
     EIK_CK(c, cudaMemcpyAsync(&bad, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     EIK_CK(c, cudaStreamSynchronize(c->stream));
     if (bad) return fail(c, EIK_EINVAL, "F must be finite and >= 0 everywhere");
     return EIK_OK;
 }
+
+// Read the validation flag of an asynchronous speed upload (waits for the
+// stream's queued work).
+eik_status check_speed(eik_ctx* c) {
+    if (!c->speed_unchecked) return EIK_OK;
+    int bad = 0;
+    EIK_CK(c, cudaMemcpyAsync(&bad, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    EIK_CK(c, cudaStreamSynchronize(c->stream));
+    c->speed_unchecked = false;
+    if (bad) {
+        c->solved = false;
+        return fail(c, EIK_EINVAL, "F must be finite and >= 0 everywhere");
+    }
+    return EIK_OK;
+}
+
+// psi of the last solve in grid order -> dst (device memory), queued on the stream.
+cudaError_t queue_result(eik_ctx* c, void* dst) {
+    if (c->prec == EIK_FP32)
+        return eikg::launch_result<float>(static_cast<const float*>(c->slot), c->stamp, static_cast<float*>(dst),
+                                          c->nx, c->ny, 0, c->nz, c->BX, c->BY, c->stream);
+    return eikg::launch_result<double>(static_cast<const double*>(c->slot), c->stamp, static_cast<double*>(dst),
+                                       c->nx, c->ny, 0, c->nz, c->BX, c->BY, c->stream);
+}
+
 
 }  // namespace
 
@@ -274,7 +311,16 @@ eik_status eik_set_speed(eik_ctx* c, const void* F, int F_on_device) {
     if (!F) return fail(c, EIK_EINVAL, "eik_set_speed: F is NULL");
     if (c->in_flight) return fail(c, EIK_ESTATE, "eik_set_speed: a solve is in flight (call eik_wait)");
     c->solved = false;
+    c->speed_unchecked = false;     // an earlier asynchronous upload is superseded
     return upload_speed(c, F, F_on_device);
+}
+
+eik_status eik_set_speed_async(eik_ctx* c, const void* F, int F_on_device) {
+    if (!c) return fail(nullptr, EIK_EINVAL, "eik_set_speed_async: ctx is NULL");
+    if (!F) return fail(c, EIK_EINVAL, "eik_set_speed_async: F is NULL");
+    if (c->in_flight) return fail(c, EIK_ESTATE, "eik_set_speed_async: a solve is in flight (call eik_wait)");
+    c->solved = false;
+    return upload_speed(c, F, F_on_device, false);
 }
 
 eik_status eik_add_sources(eik_ctx* c, int32_t n, const double* xyz) {
@@ -499,6 +545,8 @@ eik_status eik_solve_async(eik_ctx* c, const eik_params* params) {
     eik_status st = check_params(c, params);
     if (st != EIK_OK) return st;
     if (c->src.empty()) return fail(c, EIK_ESTATE, "eik_solve: no source added");
+    st = check_speed(c);
+    if (st != EIK_OK) return st;
     eik_params P = *params;
     if (P.block_dim == 0) P.block_dim = 8;
     if (P.max_restarts == 0) P.max_restarts = int64_t(1) << 24;
@@ -585,31 +633,37 @@ eik_status eik_result(eik_ctx* c, void* out, int out_on_device) {
     if (!out) return fail(c, EIK_EINVAL, "eik_result: psi_out is NULL");
     if (c->in_flight) return fail(c, EIK_ESTATE, "eik_result: a solve is in flight (call eik_wait)");
     if (!c->solved) return fail(c, EIK_ESTATE, "eik_result: no successful solve yet");
-    const size_t plane = static_cast<size_t>(c->nx) * c->ny * c->esz;
-    auto run = [&](void* dst, int z0, int z1) -> cudaError_t {
-        if (c->prec == EIK_FP32)
-            return eikg::launch_result<float>(static_cast<const float*>(c->slot), c->stamp, static_cast<float*>(dst),
-                                              c->nx, c->ny, z0, z1, c->BX, c->BY, c->stream);
-        return eikg::launch_result<double>(static_cast<const double*>(c->slot), c->stamp, static_cast<double*>(dst),
-                                           c->nx, c->ny, z0, z1, c->BX, c->BY, c->stream);
-    };
-    if (out_on_device) {
-        EIK_CK(c, run(out, 0, c->nz));
-        EIK_CK(c, cudaStreamSynchronize(c->stream));
-        return EIK_OK;
-    }
-    const size_t bytes = plane * c->nz;
-    if (bytes > c->fstage_cap) {
-        if (c->fstage) cudaFree(c->fstage);
-        c->fstage = nullptr;
-        c->fstage_cap = 0;
-        EIK_CK(c, cudaMalloc(&c->fstage, bytes));
-        c->fstage_cap = bytes;
-    }
-    EIK_CK(c, run(c->fstage, 0, c->nz));
-    EIK_CK(c, cudaMemcpyAsync(out, c->fstage, bytes, cudaMemcpyDeviceToHost, c->stream));
+    eik_status st = eik_result_async(c, out, out_on_device);
+    if (st != EIK_OK) return st;
     EIK_CK(c, cudaStreamSynchronize(c->stream));
     return EIK_OK;
+}
+
+eik_status eik_result_async(eik_ctx* c, void* out, int out_on_device) {
+    if (!c) return fail(nullptr, EIK_EINVAL, "eik_result_async: ctx is NULL");
+    if (!out) return fail(c, EIK_EINVAL, "eik_result_async: psi_out is NULL");
+    if (c->in_flight) return fail(c, EIK_ESTATE, "eik_result_async: a solve is in flight (call eik_wait)");
+    if (!c->solved) return fail(c, EIK_ESTATE, "eik_result_async: no successful solve yet");
+    if (out_on_device) {
+        EIK_CK(c, queue_result(c, out));
+        return EIK_OK;
+    }
+    const size_t bytes = static_cast<size_t>(c->nx) * c->ny * c->nz * c->esz;
+    const eik_status st = ensure_stage(c, bytes);
+    if (st != EIK_OK) return st;
+    EIK_CK(c, queue_result(c, c->fstage));
+    // the conversion is done before returning, so that work the caller queues
+    // next (another context's solve) cannot hold the SMs it needs; the copy to
+    // host memory then runs on a copy engine
+    EIK_CK(c, cudaStreamSynchronize(c->stream));
+    EIK_CK(c, cudaMemcpyAsync(out, c->fstage, bytes, cudaMemcpyDeviceToHost, c->stream));
+    return EIK_OK;
+}
+
+eik_status eik_sync(eik_ctx* c) {
+    if (!c) return fail(nullptr, EIK_EINVAL, "eik_sync: ctx is NULL");
+    EIK_CK(c, cudaStreamSynchronize(c->stream));
+    return check_speed(c);
 }
 
 void eik_destroy(eik_ctx* c) {
