@@ -80,12 +80,22 @@ __device__ void batch_restart_end(const LoopParams<T>& P) {
     }
 }
 
-// bound_band of grid D at restart k (Alg. 6 with bound_1 = stride), and of
-// restart k-1 (-1 before the first restart, so that every finite value is in
-// the first band)
-__device__ __forceinline__ double batch_bound(const SolveDesc& D, int k) { return static_cast<double>(k) * D.stride; }
-__device__ __forceinline__ double batch_bound_prev(const SolveDesc& D, int k) {
-    return k > 1 ? static_cast<double>(k - 1) * D.stride : -1.0;
+// bound_band of grid sv at restart j (Alg. 6 with bound_j = j * stride; -1 for
+// j = 0, so that every finite value is in the first band), from the table the
+// restart bookkeeping keeps three restarts ahead (read from L2: other SMs write it)
+template <typename T>
+__device__ __forceinline__ T batch_bound(const LoopParams<T>& P, int sv, int j) {
+    return __ldcg(P.gbound + static_cast<int64_t>(j % kRing) * P.nsolves + sv);
+}
+// At the end of restart k (the last warp at the barrier, every lane): the
+// bounds of restart k + 2, into the ring slot of restart k - 2
+template <typename T>
+__device__ __forceinline__ void batch_bounds_ahead(const LoopParams<T>& P, int k, int lane) {
+    const int j = k + 2;
+    for (int sv = lane; sv < P.nsolves; sv += 32)
+        P.gbound[static_cast<int64_t>(j % kRing) * P.nsolves + sv] =
+            bound_down<T>(static_cast<double>(j) * P.solves[sv].stride);
+    __threadfence();
 }
 
 template <typename T>
@@ -140,8 +150,8 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_batch_loop(LoopParams<T> P) 
                     if (warp & 4) gmask |= 16u;
                     else if (bz + 1 < D.BZ) gmask |= 32u;
                 }
-                march<T, true>(P, G, SW, warp, b, gmask, k, batch_bound_prev(D, k), batch_bound(D, k), P.window,
-                               lane, acc, early_k);
+                march<T, true>(P, G, SW, warp, b, gmask, k, batch_bound(P, sv, k - 1), batch_bound(P, sv, k), true,
+                               pick<T>(P.window, P.window_f), lane, acc, early_k);
                 if (threadIdx.x == 0) atomicMax(P.last_k + sv, k);
                 any = true;
             }
@@ -177,6 +187,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_batch_loop(LoopParams<T> P) 
                     any = false;
                     unsigned gen;
                     if (barrier_arrive(C, lane, &gen)) {
+                        batch_bounds_ahead(P, k, lane);
                         if (lane == 0) batch_restart_end<T>(P);
                         barrier_release(C, lane, gen);
                         break;
@@ -229,8 +240,8 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_batch_loop(LoopParams<T> P) 
             const int sv = __ldg(P.bsolve + b);
             const SolveDesc D = P.solves[sv];
             const Geo G{D.BX, D.BY, D.BZ, D.boff, D.GX, D.GY, D.goff, 1u};
-            march<T, false>(P, G, SW, warp, b, 0u, kk, batch_bound_prev(D, kk), batch_bound(D, kk), P.window, lane,
-                            acc, early_k || kk > k);
+            march<T, false>(P, G, SW, warp, b, 0u, kk, batch_bound(P, sv, kk - 1), batch_bound(P, sv, kk), true,
+                            pick<T>(P.window, P.window_f), lane, acc, early_k || kk > k);
             if (lane == 0) atomicMax(P.last_k + sv, kk);
             any = true;
         }
@@ -350,6 +361,7 @@ struct eik_batch {
     int32_t* d_enq = nullptr;
     int32_t* d_genq = nullptr;
     unsigned long long* d_rmin = nullptr;
+    void* gbound = nullptr;        // kRing x n bounds (LoopParams::gbound)
     int nfix = 0, nsb = 0;
     std::vector<eik_batch_tile> tuned;    // autotuned tiles (empty: none)
     int tuned_ctas = 0;
@@ -383,7 +395,7 @@ void bfree_all(eik_batch* b) {
     void* ptrs[] = {b->rr,       b->slot,     b->ups,      b->stamp,  b->queued,  b->lists,   b->done,
                     b->qgroup,   b->glists,   b->ctrl,     b->err_flag, b->d_solves, b->bsolve,
                     b->gsolve,   b->last_k,   b->tend,     b->d_fix_b, b->d_fix_p, b->d_fix_v, b->d_saved_r,
-                    b->d_sb,     b->d_enq,    b->d_genq,   b->d_rmin};
+                    b->d_sb,     b->d_enq,    b->d_genq,   b->d_rmin,   b->gbound};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -391,6 +403,23 @@ void bfree_all(eik_batch* b) {
 template <typename P>
 cudaError_t balloc(P** p, size_t bytes) {
     return cudaMalloc(reinterpret_cast<void**>(p), bytes < 16 ? 16 : bytes);
+}
+
+// bound_band of restart j with the given stride in precision T, rounded down as
+// the device's bound_down does (-1 for j = 0)
+template <typename T>
+T host_bound_down(int j, double stride);
+template <>
+float host_bound_down<float>(int j, double stride) {
+    if (j == 0) return -1.0f;
+    const double d = static_cast<double>(j) * stride;
+    float f = static_cast<float>(d);
+    if (static_cast<double>(f) > d) f = std::nextafter(f, -INFINITY);
+    return f;
+}
+template <>
+double host_bound_down<double>(int j, double stride) {
+    return j == 0 ? -1.0 : static_cast<double>(j) * stride;
 }
 
 bool tile_ok(const eik_batch_tile& t) {
@@ -571,6 +600,11 @@ eik_status batch_queue(eik_batch* b, const std::vector<eik_batch_tile>& tiles, i
         else enq.insert(enq.end(), G.enq.begin(), G.enq.end());
     }
     EIKB_CK(b, cudaMemcpyAsync(b->d_solves, D.data(), sizeof(eikg::SolveDesc) * b->n, cudaMemcpyHostToDevice, s));
+    // bounds of restarts 0-2 (the kernel writes restart k + 2's at the end of restart k)
+    std::vector<T> gb(static_cast<size_t>(eikg::kRing) * b->n);
+    for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < b->n; ++i) gb[static_cast<size_t>(j) * b->n + i] = host_bound_down<T>(j, D[i].stride);
+    EIKB_CK(b, cudaMemcpyAsync(b->gbound, gb.data(), sizeof(T) * gb.size(), cudaMemcpyHostToDevice, s));
     if (!enq.empty()) EIKB_CK(b, cudaMemcpyAsync(b->d_enq, enq.data(), enq.size() * 4, cudaMemcpyHostToDevice, s));
     if (!genq.empty())
         EIKB_CK(b, cudaMemcpyAsync(b->d_genq, genq.data(), genq.size() * 4, cudaMemcpyHostToDevice, s));
@@ -618,6 +652,7 @@ eik_status batch_queue(eik_batch* b, const std::vector<eik_batch_tile>& tiles, i
         L.qgroup = b->qgroup;
         L.ctrl = b->ctrl;
         L.window = P.window;
+        L.window_f = static_cast<float>(P.window);
         L.fallback_tau = P.fallback_tau;
         L.max_restarts = P.max_restarts;
         L.width = INFINITY;                    // full solves
@@ -628,6 +663,8 @@ eik_status batch_queue(eik_batch* b, const std::vector<eik_batch_tile>& tiles, i
         L.last_k = b->last_k;
         L.tend = b->tend;
         L.tend_cap = b->tend_cap;
+        L.gbound = static_cast<T*>(b->gbound);
+        L.nsolves = b->n;
         if (P.loop_events[0]) EIKB_CK(b, cudaEventRecord(static_cast<cudaEvent_t>(P.loop_events[0]), s));
         EIKB_CK(b, eikg::launch_batch_loop<T>(L, ctas_per_sm * b->sms, s));
         if (P.loop_events[1]) EIKB_CK(b, cudaEventRecord(static_cast<cudaEvent_t>(P.loop_events[1]), s));
@@ -922,6 +959,7 @@ eik_status eik_batch_create(eik_batch** out, int32_t n, const eik_batch_item* it
         {reinterpret_cast<void**>(&b->last_k), static_cast<size_t>(n) * 4},
         {reinterpret_cast<void**>(&b->tend), static_cast<size_t>(b->tend_cap) * 8},
         {reinterpret_cast<void**>(&b->d_rmin), static_cast<size_t>(n) * 8},
+        {&b->gbound, eikg::kRing * static_cast<size_t>(n) * b->esz},
     };
     for (auto& a : allocs) {
         e = balloc(a.p, a.bytes);

@@ -142,6 +142,7 @@ struct LoopParams {
     RestartRec* log;
     int64_t log_cap;
     double window;             // omega: acceptance window = omega * min(h/F) over the brick
+    float window_f;            // omega in single precision (FP32 marches compute the window in float)
     double fallback_tau;       // FP32: double-precision root when D < tau * k * r^2
     int64_t max_restarts;
     long long wait_limit;      // polls before a wait (barrier, list entry, neighbour march) gives up
@@ -159,6 +160,9 @@ struct LoopParams {
     int32_t* last_k;           // per grid: last restart in which one of its blocks marched
     unsigned long long* tend;  // per restart: %globaltimer at its end
     int64_t tend_cap;
+    T* gbound;                 // kRing x nsolves: bound of restart j of grid s at [j % kRing][s], rounded
+                               // down to T (-1 for j = 0); restart k's end writes j = k + 2
+    int32_t nsolves;
 };
 
 }  // namespace eikg

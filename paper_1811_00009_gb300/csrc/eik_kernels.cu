@@ -213,6 +213,11 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P
             int nm;
             next_restart_of(P, C, &ns, &nm);
             L.next_bound = fmin(L.bound + ns, P.width);         // restart k+1's bound
+            L.bound_f = __double2float_rd(L.bound);
+            L.bprev_f = __double2float_rd(L.bprev);
+            L.next_f = __double2float_rd(L.next_bound);
+            L.grow = L.bound < P.width;
+            L.grow_next = L.next_bound < P.width;
             L.early = (P.early && mode == 8 && nm == 8) ? 1 : 0;
             L.n = (mode == 8) ? __ldcg(&C->count[s]) : 0;
             L.waiting = 0;
@@ -246,7 +251,8 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P
                     if (warp & 4) gmask |= 16u;
                     else if (bz + 1 < P.BZ) gmask |= 32u;
                 }
-                march<T, true>(P, G, SW, warp, b, gmask, k, L.bprev, L.bound, P.window, lane, acc, L.early != 0);
+                march<T, true>(P, G, SW, warp, b, gmask, k, pick<T>(L.bprev, L.bprev_f), pick<T>(L.bound, L.bound_f),
+                               L.grow != 0, pick<T>(P.window, P.window_f), lane, acc, L.early != 0);
                 any = true;
             }
         }
@@ -320,8 +326,12 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P
                 }
             }
             __syncwarp();
-            march<T, false>(P, G, SW, warp, b, 0u, kk, kk > k ? L.bound : L.bprev, kk > k ? L.next_bound : L.bound,
-                            P.window, lane, acc, L.early != 0 || kk > k);
+            const bool ahead = kk > k;
+            march<T, false>(P, G, SW, warp, b, 0u, kk,
+                            ahead ? pick<T>(L.bound, L.bound_f) : pick<T>(L.bprev, L.bprev_f),
+                            ahead ? pick<T>(L.next_bound, L.next_f) : pick<T>(L.bound, L.bound_f),
+                            (ahead ? L.grow_next : L.grow) != 0, pick<T>(P.window, P.window_f), lane, acc,
+                            L.early != 0 || ahead);
             any = true;
         }
         if (__ldcg(&C->done)) return;

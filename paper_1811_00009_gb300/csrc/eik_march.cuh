@@ -142,6 +142,15 @@ __device__ __forceinline__ float bound_down<float>(double b) { return __double2f
 template <>
 __device__ __forceinline__ double bound_down<double>(double b) { return b; }
 
+// The value of precision T among a double and its single-precision copy
+// (prepared once per restart, so that marches do no double arithmetic).
+template <typename T>
+__device__ __forceinline__ T pick(double d, float f);
+template <>
+__device__ __forceinline__ float pick<float>(double, float f) { return f; }
+template <>
+__device__ __forceinline__ double pick<double>(double d, float) { return d; }
+
 template <typename T>
 struct RootOf;
 template <>
@@ -337,12 +346,10 @@ __device__ __forceinline__ void enqueue_next(const LoopParams<T>& P, const Geo& 
 // one block of the paper.
 template <typename T, bool GROUP>
 __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int warp, int32_t b, unsigned gmask,
-                      int k, double bprev_d, double bound_d, double window, int lane, MarchAcc& acc, bool publish) {
-    __shared__ double s_wmin[kWarps];
+                      int k, T bprev, T bound, bool grow, T window, int lane, MarchAcc& acc, bool publish) {
+    __shared__ T s_wmin[kWarps];
     WarpSmem<T>& S = SW[warp];
     const T INF = Num<T>::inf();
-    const T bprev = bound_down<T>(bprev_d);
-    const T bound = bound_down<T>(bound_d);
     const bool present = b >= 0;
     const int y = lane & 7, zp = lane >> 3, z0 = 2 * zp;
     const int BX = G.BX, BY = G.BY, BZ = G.BZ;
@@ -502,15 +509,15 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
     T w;
     if constexpr (GROUP) {
         // one window for the group: omega times the smallest h/F of its bricks
-        if (lane == 0) s_wmin[warp] = static_cast<double>(rmin_b);
+        if (lane == 0) s_wmin[warp] = rmin_b;
         __syncthreads();
-        double g = s_wmin[0];
+        T g = s_wmin[0];
 #pragma unroll
-        for (int i = 1; i < kWarps; ++i) g = fmin(g, s_wmin[i]);
-        w = static_cast<T>(window * g);
+        for (int i = 1; i < kWarps; ++i) g = vmin(g, s_wmin[i]);
+        w = window * g;
         __syncthreads();
     } else {
-        w = static_cast<T>(window * static_cast<double>(rmin_b));
+        w = window * rmin_b;
     }
     const float tau = static_cast<float>(P.fallback_tau);
 
@@ -604,12 +611,12 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
             T lmin = INF;
             for (int i = lane; i < n; i += 32) lmin = vmin(lmin, vabs(S.psi[S.band[i]]));
             T mn = warp_min_nn(lmin);
-            if (lane == 0) s_wmin[warp] = static_cast<double>(mn);
+            if (lane == 0) s_wmin[warp] = mn;
             __syncthreads();
-            double g = s_wmin[0];
+            T g = s_wmin[0];
 #pragma unroll
-            for (int i = 1; i < kWarps; ++i) g = fmin(g, s_wmin[i]);
-            mn = static_cast<T>(g);
+            for (int i = 1; i < kWarps; ++i) g = vmin(g, s_wmin[i]);
+            mn = g;
             __syncthreads();
             if (!(mn < INF) || !(mn <= bound)) break;   // band empty, or its minimum above the bound
             if (++rounds > kRoundCap) {
@@ -818,7 +825,7 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
 
     // ---- activation for restart k+1 (A of Alg. 4/5, C of Alg. 4)
     // (once the bound has reached width_band, pending nodes above it stay tentative: Alg. 6's A flag)
-    if (lane == 6 && n > 0 && bound_d < P.width) enqueue_next(P, G, k, b);
+    if (lane == 6 && n > 0 && grow) enqueue_next(P, G, k, b);
     if (lane < 6 && um[lane] != 0ull && nbr[lane] >= 0) enqueue_next(P, G, k, nbr[lane]);
     if (lane == 0) acc.band += n;
     // publish: the brick's restart-k march has finished (read by early marches
@@ -914,6 +921,8 @@ __device__ __forceinline__ void flush_acc(Ctrl* C, MarchAcc& acc, int lane) {
 // the march needs every register it can get.
 struct LoopState {
     double bound, bprev, next_bound;
+    float bound_f, bprev_f, next_f;    // the same rounded down to single precision
+    int grow, grow_next;       // bound, next_bound below width_band (pending nodes re-activate the block)
     int n;                     // length of this restart's brick list
     int early;                 // early work allowed while waiting at this restart's barrier
     int waiting;               // arrived at the barrier

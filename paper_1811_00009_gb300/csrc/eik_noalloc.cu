@@ -319,6 +319,7 @@ eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float* F, in
         L.log = nullptr;
         L.log_cap = 0;
         L.window = P.window;
+        L.window_f = static_cast<float>(P.window);
         L.width = P.width;
         L.fallback_tau = P.fallback_tau;
         L.max_restarts = P.max_restarts;

@@ -498,6 +498,7 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
         L.log = P.log_restarts ? c->log : nullptr;
         L.log_cap = P.log_restarts ? c->log_cap : 0;
         L.window = P.window;
+        L.window_f = static_cast<float>(P.window);
         L.fallback_tau = P.fallback_tau;
         L.max_restarts = P.max_restarts;
         L.width = P.width;
