@@ -22,16 +22,18 @@ namespace eikg {
 __device__ inline void schedule_features(float* x, double active, double band, double accepted, double solves,
                                          double rmin, double rmax, double bound, double stride, int k, int mode,
                                          double h, int nmax) {
-    x[0] = static_cast<float>(log1p(active) / 16.0);
-    x[1] = static_cast<float>(log1p(band) / 20.0);
-    x[2] = static_cast<float>(log1p(accepted) / 20.0);
-    x[3] = (rmin > 0.0 && rmin < 1e300) ? static_cast<float>(log(h / rmin)) : 0.0f;
-    x[4] = (rmax > 0.0 && rmax < 1e300) ? static_cast<float>(log(h / rmax)) : 0.0f;
-    x[5] = static_cast<float>(bound / (h * nmax));
-    x[6] = static_cast<float>(log1p(static_cast<double>(k)) / 8.0);
-    x[7] = static_cast<float>(stride / h / 4.0);
+    // single precision throughout (the network is FP32; double logs are slow on this part)
+    const float hf = static_cast<float>(h);
+    x[0] = log1pf(static_cast<float>(active)) / 16.0f;
+    x[1] = log1pf(static_cast<float>(band)) / 20.0f;
+    x[2] = log1pf(static_cast<float>(accepted)) / 20.0f;
+    x[3] = (rmin > 0.0 && rmin < 1e300) ? logf(hf / static_cast<float>(rmin)) : 0.0f;
+    x[4] = (rmax > 0.0 && rmax < 1e300) ? logf(hf / static_cast<float>(rmax)) : 0.0f;
+    x[5] = static_cast<float>(bound) / (hf * static_cast<float>(nmax));
+    x[6] = log1pf(static_cast<float>(k)) / 8.0f;
+    x[7] = static_cast<float>(stride) / hf / 4.0f;
     x[8] = (mode == 16) ? 1.0f : 0.0f;
-    x[9] = static_cast<float>(log1p(solves) / 20.0);
+    x[9] = log1pf(static_cast<float>(solves)) / 20.0f;
     for (int i = 0; i < kIn; ++i) {
         if (!(x[i] == x[i])) x[i] = 0.0f;
         x[i] = fminf(10.0f, fmaxf(-10.0f, x[i]));
@@ -67,10 +69,14 @@ __device__ __forceinline__ void next_restart_of(const LoopParams<T>& P, const Ct
 // last): statistics, exit test and the next bound of Alg. 6 (restart k+1 takes
 // the action chosen at the end of restart k-1) and, for the learned schedule,
 // the schedule network (one hidden unit per lane) choosing the stride and
-// block edge of restart k+2 from the front after restart k.
+// block edge of restart k+2 from the front after restart k.  `scratch` is the
+// calling warp's shared tile (free while it waits at the barrier): the
+// network's weights are staged there with coalesced loads.
 template <typename T>
-__device__ void restart_end(const LoopParams<T>& P, int lane) {
+__device__ void restart_end(const LoopParams<T>& P, int lane, float* scratch) {
     static_assert(kHid == 32, "one hidden unit per lane");
+    static_assert(sizeof(WarpSmem<T>) >= (kHid * (kIn + 1) + (kHid + kAct) * (kHid + 1)) * sizeof(float),
+                  "the staged weights fit the warp's tile");
     __shared__ float s_x[kIn];
     __shared__ float s_h1[kHid];
     __shared__ float s_h2[kHid];
@@ -89,18 +95,29 @@ __device__ void restart_end(const LoopParams<T>& P, int lane) {
                           __ldcg(&C->stride), k, mode, P.h, P.nmax);
     __syncwarp();
     if (P.sched == 1 && P.mlp != nullptr) {
-        const float* w = P.mlp;
-        float a = w[kOffB1 + lane];
-        for (int j = 0; j < kIn; ++j) a += w[kOffW1 + lane * kIn + j] * s_x[j];
+        // weight rows staged with a padded stride (11 and 33 floats), so that
+        // the 32 lanes, one hidden unit each, read 32 different banks
+        constexpr int kS1 = kIn + 1, kS2 = kHid + 1;
+        float* w1 = scratch;
+        float* w2 = w1 + kHid * kS1;
+        float* w3 = w2 + kHid * kS2;
+        for (int i = lane; i < kHid * kIn; i += 32) w1[(i / kIn) * kS1 + i % kIn] = __ldg(P.mlp + kOffW1 + i);
+        for (int i = lane; i < kHid * kHid; i += 32) w2[(i >> 5) * kS2 + (i & 31)] = __ldg(P.mlp + kOffW2 + i);
+        for (int i = lane; i < kAct * kHid; i += 32) w3[(i >> 5) * kS2 + (i & 31)] = __ldg(P.mlp + kOffW3 + i);
+        const float b1 = __ldg(P.mlp + kOffB1 + lane), b2 = __ldg(P.mlp + kOffB2 + lane);
+        const float b3 = lane < kAct ? __ldg(P.mlp + kOffB3 + lane) : 0.0f;
+        __syncwarp();
+        float a = b1;
+        for (int j = 0; j < kIn; ++j) a += w1[lane * kS1 + j] * s_x[j];
         s_h1[lane] = tanhf(a);
         __syncwarp();
-        a = w[kOffB2 + lane];
-        for (int j = 0; j < kHid; ++j) a += w[kOffW2 + lane * kHid + j] * s_h1[j];
+        a = b2;
+        for (int j = 0; j < kHid; ++j) a += w2[lane * kS2 + j] * s_h1[j];
         s_h2[lane] = tanhf(a);
         __syncwarp();
         if (lane < kAct) {
-            a = w[kOffB3 + lane];
-            for (int j = 0; j < kHid; ++j) a += w[kOffW3 + lane * kHid + j] * s_h2[j];
+            a = b3;
+            for (int j = 0; j < kHid; ++j) a += w3[lane * kS2 + j] * s_h2[j];
             s_y[lane] = a;
         }
         __syncwarp();
@@ -281,7 +298,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P
                     any = false;
                     unsigned gen;
                     if (barrier_arrive(C, lane, &gen)) {
-                        restart_end<T>(P, lane);
+                        restart_end<T>(P, lane, reinterpret_cast<float*>(SW + warp));
                         barrier_release(C, lane, gen);
                         break;
                     }
