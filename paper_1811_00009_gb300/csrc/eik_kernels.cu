@@ -140,7 +140,9 @@ __device__ void restart_end(const LoopParams<T>& P, int lane, float* scratch) {
     } else if (P.sched == 2) {
         action = static_cast<int>(mix32(P.seed * 0x9e3779b9u + static_cast<unsigned>(k)) % kAct);
     }
-    const int n_next = (next_mode == 16) ? __ldcg(&C->gcount[s1]) : __ldcg(&C->count[s1]);
+    // work for restart k+1: its brick list, or its group list (which a learned or
+    // random schedule builds from the brick list only when the restart starts)
+    const int n_next = __ldcg(&C->count[s1]) + ((next_mode == 16) ? __ldcg(&C->gcount[s1]) : 0);
     const unsigned long long now = globaltimer();
     const unsigned long long acc_a = __ldcg(&C->r_accepted), acc_band = __ldcg(&C->r_band);
     const unsigned long long acc_s = __ldcg(&C->r_solves);
@@ -200,6 +202,25 @@ __device__ void restart_end(const LoopParams<T>& P, int lane, float* scratch) {
     }
 }
 
+// Restart k's group list (ring slot s) from its brick list, by every thread of
+// the launch, then a grid barrier; false if a wait ran out.  Out of line: it
+// runs only at 16^3 restarts of a learned or random schedule.
+__device__ __noinline__ bool groups_from_bricks(Ctrl* C, const int32_t* list, int32_t* qgroup, int32_t* glist, int s,
+                                                int k, int BX, int BY, int GX, int GY, int lane, long long limit) {
+    const int nb = __ldcg(&C->count[s]);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
+        const int32_t x = __ldcg(list + i);
+        const int bx = x % BX, by = (x / BX) % BY, bz = x / (BX * BY);
+        const int32_t g = ((bz >> 1) * GY + (by >> 1)) * GX + (bx >> 1);
+        if (atomicMax(qgroup + g, k) < k) {
+            const int pos = atomicAdd(&C->gcount[s], 1);
+            glist[pos] = g;
+        }
+    }
+    __threadfence();
+    return grid_sync(C, lane, limit);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -209,7 +230,11 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P
     WarpSmem<T>* SW = reinterpret_cast<WarpSmem<T>*>(smem_raw);
     LoopState& L = s_state[warp];              // the loop's bookkeeping, kept out of registers
     Ctrl* C = P.ctrl;
-    const Geo G{P.BX, P.BY, P.BZ, 0, P.GX, P.GY, 0, 1u | (P.groups ? 2u : 0u)};
+    // Work lists the marches fill: the brick list, and for fixed 16^3 blocks
+    // the group list too.  Under a learned or random schedule a 16^3 restart
+    // builds its group list from its brick list when it starts (such restarts
+    // are rare, and every enqueue would otherwise pay for the group list).
+    const Geo G{P.BX, P.BY, P.BZ, 0, P.GX, P.GY, 0, (P.groups && P.sched == 0) ? 3u : 1u};
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const unsigned long long t0 = globaltimer();
         C->t_begin = t0;
@@ -243,6 +268,10 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P
         }
         __syncwarp();
         if (mode == 16) {
+            if (!(G.lists & 2u) &&
+                !groups_from_bricks(C, P.list[s], P.qgroup + static_cast<int64_t>(s) * P.ngroups, P.glist[s], s, k,
+                                    P.BX, P.BY, P.GX, P.GY, lane, P.wait_limit))
+                return;
             // one CTA per group of 2x2x2 bricks
             const int n = __ldcg(&C->gcount[s]);
             for (;;) {

@@ -967,6 +967,28 @@ __device__ __forceinline__ int barrier_poll(Ctrl* C, int lane, unsigned gen) {
     return __shfl_sync(0xffffffffu, state, 0);
 }
 
+// A grid barrier inside a restart (no bookkeeping): every warp of the launch
+// arrives; false if this or another wait ran out (the status then says so).
+__device__ inline bool grid_sync(Ctrl* C, int lane, long long limit) {
+    unsigned gen;
+    if (barrier_arrive(C, lane, &gen)) {
+        barrier_release(C, lane, gen);
+        return true;
+    }
+    unsigned nap = 32;
+    for (long long it = 0;; ++it) {
+        const int st = barrier_poll(C, lane, gen);
+        if (st == 1) return true;
+        if (st == 2) return false;
+        if (it > limit) {
+            if (lane == 0) atomicOr(&C->status, kStWaitTimeout);
+            return false;
+        }
+        __nanosleep(nap);
+        if (nap < 1024) nap <<= 1;
+    }
+}
+
 // While waiting at the barrier of restart k: the next entry of restart k+1's
 // list (ring slot s1) for an early march, or -1.  A warp claims one index
 // (atomicAdd on the slot's head) and keeps the claim until the list holds that
