@@ -753,10 +753,10 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
                 const unsigned km = __ballot_sync(kFull, keep);
                 if (keep) S.band[kept + __popc(km & lt)] = static_cast<uint16_t>(hh);
                 kept += __popc(km);
-                acc.accepted += take ? 1u : 0u;
                 hh = hh2;
                 v = v2;
             }
+            if (lane == 0) acc.accepted += static_cast<unsigned>(n - kept);   // every entry is taken or kept
             n = kept;
             __syncwarp();
             // neighbours of the accepted nodes (Alg. 2) that are solved
