@@ -29,7 +29,7 @@
 namespace eikg {
 
 template <typename T>
-cudaError_t launch_layout_speed(const T*, T*, int, int, int, int, int, int64_t, double, int*, cudaStream_t);
+cudaError_t launch_layout_speed(const T*, T*, int, int, int, int, int, int64_t, double, int*, int, cudaStream_t);
 template <typename T>
 cudaError_t launch_init_sources(int, const int32_t*, const int32_t*, const double*, int, const int32_t*, int,
                                 const int32_t*, int, const int32_t*, T*, unsigned long long*, unsigned long long*,
@@ -460,7 +460,7 @@ eik_status batch_setup(eik_batch* b, const eik_batch_item* items) {
         }
         T* rr = static_cast<T*>(b->rr) + static_cast<int64_t>(G.geo.boff) * kBrick;
         cudaError_t e = eikg::launch_layout_speed<T>(static_cast<const T*>(Fd), rr, G.nx, G.ny, G.nz, G.geo.BX,
-                                                     G.geo.BY, G.nb, G.h, b->err_flag, s);
+                                                     G.geo.BY, G.nb, G.h, b->err_flag, 1, s);
         if (e == cudaSuccess) {
             const int rg = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(1024, (G.nb * kBrick + 255) / 256)));
             eikg::k_rmin<T><<<rg, 256, 0, s>>>(rr, G.nb * kBrick, b->d_rmin + i);

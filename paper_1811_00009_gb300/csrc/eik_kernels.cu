@@ -387,24 +387,28 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P
 // F (x fastest) -> h/F in brick layout; flags negative, NaN or infinite speeds.
 template <typename T>
 __global__ void k_layout_speed(const T* __restrict__ F, T* __restrict__ rr, int nx, int ny, int nz, int BX,
-                               int BY, int64_t nbricks, double h, int* err) {
+                               int BY, int64_t nbricks, double h, int* err, int seq) {
     const int64_t total = nbricks * kBrick;
     const T INF = Num<T>::inf();
+    // h/F in the working precision: one IEEE division in FP32 mode (a double
+    // division per node would make this copy kernel FP64-bound on this part)
+    const T hT = static_cast<T>(h);
+    int bad = 0;
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
          t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t b = t >> 9;
+        const int b = static_cast<int>(t >> 9);                 // brick indices fit in 32 bits
         const int p = static_cast<int>(t & 511);
-        const int bx = static_cast<int>(b % BX), by = static_cast<int>((b / BX) % BY),
-                  bz = static_cast<int>(b / (static_cast<int64_t>(BX) * BY));
+        const int bx = b % BX, byz = b / BX, by = byz % BY, bz = byz / BY;
         const int i = bx * 8 + (p & 7), j = by * 8 + ((p >> 3) & 7), k = bz * 8 + (p >> 6);
         T r = INF;
         if (i < nx && j < ny && k < nz) {
-            const T f = F[(static_cast<int64_t>(k) * ny + j) * nx + i];
-            if (!(f >= 0) || !(f < INF)) atomicOr(err, 1);
-            else if (f > 0) r = static_cast<T>(h / static_cast<double>(f));
+            const T f = __ldg(F + (static_cast<int64_t>(k) * ny + j) * nx + i);
+            if (!(f >= 0) || !(f < INF)) bad = 1;
+            else if (f > 0) r = hT / f;
         }
-        rr[t] = r;
+        __stcs(rr + t, r);
     }
+    if (bad) *reinterpret_cast<volatile int*>(err) = seq;     // this upload's number marks a bad F
 }
 
 // Alg. 1 for the bricks that hold fixed nodes, and the work list of restart 1.
@@ -470,17 +474,19 @@ template <typename T>
 __global__ void k_result(const T* __restrict__ slot, const unsigned long long* __restrict__ stamp, T* __restrict__ out, int nx,
                          int ny, int z_begin, int z_end, int BX, int BY) {
     const T INF = Num<T>::inf();
-    const int64_t plane = static_cast<int64_t>(nx) * ny;
-    const int64_t total = plane * (z_end - z_begin);
-    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
-         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int k = z_begin + static_cast<int>(t / plane);
-        const int64_t rem = t % plane;
-        const int j = static_cast<int>(rem / nx), i = static_cast<int>(rem % nx);
-        const int64_t b = (static_cast<int64_t>(k >> 3) * BY + (j >> 3)) * BX + (i >> 3);
-        const int p = ((k & 7) * 8 + (j & 7)) * 8 + (i & 7);
-        const unsigned long long st = stamp[b];
-        out[t] = (st == kUntouched) ? INF : slot[(b * 2 + stamp_copy(st)) * kSlot + p];
+    // one block per grid row (k, j) at a time, its threads along x: 32-bit row
+    // arithmetic, coalesced stores, 32-byte runs of each brick row read
+    const int rows = ny * (z_end - z_begin);
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int kk = r / ny, j = r - kk * ny, k = z_begin + kk;
+        const int64_t brow = (static_cast<int64_t>(k >> 3) * BY + (j >> 3)) * BX;
+        const int prow = ((k & 7) * 8 + (j & 7)) * 8;
+        T* o = out + static_cast<int64_t>(r) * nx;
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const int64_t b = brow + (i >> 3);
+            const unsigned long long st = __ldg(stamp + b);
+            o[i] = (st == kUntouched) ? INF : __ldcs(slot + (b * 2 + stamp_copy(st)) * kSlot + prow + (i & 7));
+        }
     }
 }
 
@@ -489,11 +495,11 @@ __global__ void k_result(const T* __restrict__ slot, const unsigned long long* _
 // ---------------------------------------------------------------------------
 template <typename T>
 cudaError_t launch_layout_speed(const T* F, T* rr, int nx, int ny, int nz, int BX, int BY, int64_t nbricks,
-                                double h, int* err, cudaStream_t s) {
+                                double h, int* err, int seq, cudaStream_t s) {
     const int64_t total = nbricks * kBrick;
     int grid = static_cast<int>((total + 255) / 256);
     if (grid > 65535 * 4) grid = 65535 * 4;
-    k_layout_speed<T><<<grid, 256, 0, s>>>(F, rr, nx, ny, nz, BX, BY, nbricks, h, err);
+    k_layout_speed<T><<<grid, 256, 0, s>>>(F, rr, nx, ny, nz, BX, BY, nbricks, h, err, seq);
     return cudaGetLastError();
 }
 
@@ -530,9 +536,8 @@ cudaError_t launch_gather_r(int n, const int32_t* nb_b, const int32_t* nb_p, con
 template <typename T>
 cudaError_t launch_result(const T* slot, const unsigned long long* stamp, T* out, int nx, int ny, int z_begin, int z_end,
                           int BX, int BY, cudaStream_t s) {
-    const int64_t total = static_cast<int64_t>(nx) * ny * (z_end - z_begin);
-    int grid = static_cast<int>((total + 255) / 256);
-    if (grid > 65535 * 4) grid = 65535 * 4;
+    const int64_t rows = static_cast<int64_t>(ny) * (z_end - z_begin);
+    int grid = static_cast<int>(rows < 65535 * 4 ? rows : 65535 * 4);
     if (grid < 1) grid = 1;
     k_result<T><<<grid, 256, 0, s>>>(slot, stamp, out, nx, ny, z_begin, z_end, BX, BY);
     return cudaGetLastError();
@@ -562,7 +567,7 @@ cudaError_t launch_restart_loop(const LoopParams<T>& P, int grid, cudaStream_t s
 
 #define EIKG_INSTANTIATE(T)                                                                                     \
     template cudaError_t launch_layout_speed<T>(const T*, T*, int, int, int, int, int, int64_t, double, int*,    \
-                                                cudaStream_t);                                                   \
+                                                int, cudaStream_t);                                              \
     template cudaError_t launch_init_sources<T>(int, const int32_t*, const int32_t*, const double*, int,         \
                                                 const int32_t*, int, const int32_t*, int, const int32_t*, T*,     \
                                                 unsigned long long*, unsigned long long*, int32_t*, int32_t*, T*,  \

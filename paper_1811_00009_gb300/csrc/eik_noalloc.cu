@@ -27,7 +27,7 @@
 
 namespace eikg {
 template <typename T>
-cudaError_t launch_layout_speed(const T*, T*, int, int, int, int, int, int64_t, double, int*, cudaStream_t);
+cudaError_t launch_layout_speed(const T*, T*, int, int, int, int, int, int64_t, double, int*, int, cudaStream_t);
 template <typename T>
 cudaError_t launch_init_sources(int, const int32_t*, const int32_t*, const double*, int, const int32_t*, int,
                                 const int32_t*, int, const int32_t*, T*, unsigned long long*, unsigned long long*,
@@ -195,7 +195,7 @@ eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float* F, in
     // speeds -> h/F in brick layout, with validation
     int bad = 0;
     NA_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
-    NA_CK(eikg::launch_layout_speed<float>(F, rr, nx, ny, nz, BX, BY, nb, h, err, st));
+    NA_CK(eikg::launch_layout_speed<float>(F, rr, nx, ny, nz, BX, BY, nb, h, err, 1, st));
     NA_CK(cudaMemcpyAsync(&bad, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     // fixed nodes: the nodes of each source's cell, psi0 = distance / F
     double cd[kMaxFix];

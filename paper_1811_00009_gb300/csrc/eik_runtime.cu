@@ -20,7 +20,7 @@
 
 namespace eikg {
 template <typename T>
-cudaError_t launch_layout_speed(const T*, T*, int, int, int, int, int, int64_t, double, int*, cudaStream_t);
+cudaError_t launch_layout_speed(const T*, T*, int, int, int, int, int, int64_t, double, int*, int, cudaStream_t);
 template <typename T>
 cudaError_t launch_init_sources(int, const int32_t*, const int32_t*, const double*, int, const int32_t*, int,
                                 const int32_t*, int, const int32_t*, T*, unsigned long long*, unsigned long long*,
@@ -62,7 +62,18 @@ struct eik_ctx {
     int32_t* qgroup = nullptr;     // kRing x ngroups
     int32_t* glists = nullptr;     // kRing x ngroups
     eikg::Ctrl* ctrl = nullptr;
-    int* err_flag = nullptr;
+    int* err_flag = nullptr;       // unused: speeds are checked through h_err
+    // Mapped pinned host memory that kernels write directly, so that the host
+    // reads small results after a stream synchronisation without a
+    // device-to-host copy (which would queue behind another context's large
+    // result copy on the copy engine)
+    int* h_err = nullptr;          // number of the last upload that found a bad F
+    int* d_err = nullptr;
+    int upload_seq = 0;
+    int check_seq = 0;             // upload whose flag is still to be read (speed_unchecked)
+    double* h_gather = nullptr;    // h/F at the source candidates
+    double* d_gather = nullptr;
+    int gather_cap = 0;
     float* d_mlp = nullptr;        // schedule network weights (eik_set_schedule)
     eikg::RestartRec* log = nullptr;
     int64_t log_cap = 0;
@@ -114,6 +125,8 @@ void free_all(eik_ctx* c) {
                     c->ctrl,  c->err_flag, c->log, c->scratch, c->fstage, c->d_mlp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (c->h_err) cudaFreeHost(c->h_err);
+    if (c->h_gather) cudaFreeHost(c->h_gather);
 }
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
@@ -129,6 +142,8 @@ eik_status ensure_stage(eik_ctx* c, size_t bytes) {
     return EIK_OK;
 }
 
+eik_status check_speed(eik_ctx* c);
+
 // F (x fastest, caller memory) -> h/F in brick layout, with validation (checked
 // here, or left for check_speed when `wait` is false).
 eik_status upload_speed(eik_ctx* c, const void* F, int F_on_device, bool wait = true) {
@@ -140,33 +155,27 @@ eik_status upload_speed(eik_ctx* c, const void* F, int F_on_device, bool wait = 
         EIK_CK(c, cudaMemcpyAsync(c->fstage, F, bytes, cudaMemcpyHostToDevice, c->stream));
         Fd = c->fstage;
     }
-    EIK_CK(c, cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->stream));
+    const int seq = ++c->upload_seq;
     if (c->prec == EIK_FP32)
         EIK_CK(c, eikg::launch_layout_speed<float>(static_cast<const float*>(Fd), static_cast<float*>(c->rr), c->nx,
-                                                   c->ny, c->nz, c->BX, c->BY, c->nbricks, c->h, c->err_flag,
+                                                   c->ny, c->nz, c->BX, c->BY, c->nbricks, c->h, c->d_err, seq,
                                                    c->stream));
     else
         EIK_CK(c, eikg::launch_layout_speed<double>(static_cast<const double*>(Fd), static_cast<double*>(c->rr),
                                                     c->nx, c->ny, c->nz, c->BX, c->BY, c->nbricks, c->h,
-                                                    c->err_flag, c->stream));
-    if (!wait) {
-        c->speed_unchecked = true;
-        return EIK_OK;
-    }
-    int bad = 0;
-    EIK_CK(c, cudaMemcpyAsync(&bad, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    EIK_CK(c, cudaStreamSynchronize(c->stream));
-    if (bad) return fail(c, EIK_EINVAL, "F must be finite and >= 0 everywhere");
-    return EIK_OK;
+                                                    c->d_err, seq, c->stream));
+    c->speed_unchecked = true;
+    c->check_seq = seq;
+    if (!wait) return EIK_OK;
+    return check_speed(c);
 }
 
 // Read the validation flag of an asynchronous speed upload (waits for the
 // stream's queued work).
 eik_status check_speed(eik_ctx* c) {
     if (!c->speed_unchecked) return EIK_OK;
-    int bad = 0;
-    EIK_CK(c, cudaMemcpyAsync(&bad, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     EIK_CK(c, cudaStreamSynchronize(c->stream));
+    const bool bad = *reinterpret_cast<volatile int*>(c->h_err) == c->check_seq;
     c->speed_unchecked = false;
     if (bad) {
         c->solved = false;
@@ -274,6 +283,10 @@ eik_status eik_create(eik_ctx** out, const int32_t dims[3], double h, const void
             return bail(EIK_ENOMEM, std::string("eik_create: cudaMalloc of ") + std::to_string(a.bytes) +
                                         " bytes failed: " + cudaGetErrorString(e));
     }
+    e = cudaHostAlloc(reinterpret_cast<void**>(&c->h_err), 64, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->d_err), c->h_err, 0);
+    if (e != cudaSuccess) return bail(EIK_ENOMEM, std::string("eik_create: mapped host flag: ") + cudaGetErrorString(e));
+    *c->h_err = 0;
     {
         const eik_status st = upload_speed(c, F, F_on_device);
         if (st != EIK_OK) {
@@ -386,14 +399,23 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
     };
     int32_t* d_cb = reinterpret_cast<int32_t*>(carve(nc * 4));
     int32_t* d_cp = reinterpret_cast<int32_t*>(carve(nc * 4));
-    double* d_cr = reinterpret_cast<double*>(carve(nc * 8));
+    carve(nc * 8);
     std::vector<double> cr(nc);
     if (nc > 0) {
+        if (nc > c->gather_cap) {
+            if (c->h_gather) cudaFreeHost(c->h_gather);
+            c->h_gather = nullptr;
+            c->gather_cap = 0;
+            EIK_CK(c, cudaHostAlloc(reinterpret_cast<void**>(&c->h_gather), static_cast<size_t>(nc) * 8,
+                                    cudaHostAllocMapped));
+            EIK_CK(c, cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->d_gather), c->h_gather, 0));
+            c->gather_cap = nc;
+        }
         EIK_CK(c, cudaMemcpyAsync(d_cb, cb.data(), nc * 4, cudaMemcpyHostToDevice, s));
         EIK_CK(c, cudaMemcpyAsync(d_cp, cp.data(), nc * 4, cudaMemcpyHostToDevice, s));
-        EIK_CK(c, eikg::launch_gather_r<T>(nc, d_cb, d_cp, static_cast<const T*>(c->rr), d_cr, s));
-        EIK_CK(c, cudaMemcpyAsync(cr.data(), d_cr, nc * 8, cudaMemcpyDeviceToHost, s));
+        EIK_CK(c, eikg::launch_gather_r<T>(nc, d_cb, d_cp, static_cast<const T*>(c->rr), c->d_gather, s));
         EIK_CK(c, cudaStreamSynchronize(s));
+        for (int t = 0; t < nc; ++t) cr[t] = reinterpret_cast<volatile double*>(c->h_gather)[t];
     }
     const std::vector<eikh::FixNode> uf = eikh::fixed_nodes(cand, cr, c->h);
     std::vector<int32_t> sb, enq;
