@@ -51,6 +51,10 @@ __device__ __forceinline__ unsigned ubits(float v) { return __float_as_uint(v); 
 __device__ __forceinline__ unsigned long long ubits(double v) {
     return static_cast<unsigned long long>(__double_as_longlong(v));
 }
+__device__ __forceinline__ float from_bits(unsigned u) { return __uint_as_float(u); }
+__device__ __forceinline__ double from_bits(unsigned long long u) {
+    return __longlong_as_double(static_cast<long long>(u));
+}
 __device__ __forceinline__ float vabs(float v) { return fabsf(v); }
 __device__ __forceinline__ double vabs(double v) { return fabs(v); }
 __device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
@@ -559,11 +563,17 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
                 // KNOWN neighbours below the node's current value (Alg. 3's test): as
                 // unsigned bit patterns every KNOWN (sign clear) value orders as its
                 // value and every BAND value (sign set) lies above any KNOWN one
+                // (per axis: the smaller bit pattern of the two neighbours is the
+                // smaller KNOWN value if either is KNOWN; it counts if below c)
                 const auto cb = ubits(c);
-                auto kn = [&](T v) -> T { return ubits(v) < cb ? v : INF; };
-                T mx = vmin(kn(S.psi[hq - 1]), kn(S.psi[hq + 1]));
-                T my = vmin(kn(S.psi[hq - 10]), kn(S.psi[hq + 10]));
-                T mz = vmin(kn(S.psi[hq - 100]), kn(S.psi[hq + 100]));
+                auto axis = [&](T a, T b) -> T {
+                    const auto ua = ubits(a), ub = ubits(b);
+                    const auto m = ua < ub ? ua : ub;
+                    return m < cb ? from_bits(m) : INF;
+                };
+                T mx = axis(S.psi[hq - 1], S.psi[hq + 1]);
+                T my = axis(S.psi[hq - 10], S.psi[hq + 10]);
+                T mz = axis(S.psi[hq - 100], S.psi[hq + 100]);
                 // reorder psi_1 <= psi_2 <= psi_3
                 T lo = vmin(mx, my), hi = vmax(mx, my);
                 T a0 = vmin(lo, mz);
