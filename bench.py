@@ -36,7 +36,7 @@ KERNELS_PER_SOLVE = 4                                # gather_r, init_sources, r
 # DRAM bytes of one k_restart_loop launch on the 1024^3 workload (fixed stride 2h, 8^3 blocks, FP32) from a
 # one-pass ncu capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum = 93.12 GB + 53.34 GB),
 # per node; profiles/launches_c4_1024_fixed2h.md gives the command.
-NCU_TRAFFIC_PER_NODE = {"fp32": (93.02e9 + 53.25e9) / 1024 ** 3}
+NCU_TRAFFIC_PER_NODE = {"fp32": (93.10e9 + 53.34e9) / 1024 ** 3}
 
 
 def measured_peaks():
