@@ -62,7 +62,6 @@ struct eik_ctx {
     int32_t* qgroup = nullptr;     // kRing x ngroups
     int32_t* glists = nullptr;     // kRing x ngroups
     eikg::Ctrl* ctrl = nullptr;
-    int* err_flag = nullptr;       // unused: speeds are checked through h_err
     // Mapped pinned host memory that kernels write directly, so that the host
     // reads small results after a stream synchronisation without a
     // device-to-host copy (which would queue behind another context's large
@@ -122,7 +121,7 @@ cudaError_t dalloc(P** p, size_t bytes) {
 
 void free_all(eik_ctx* c) {
     void* ptrs[] = {c->rr,    c->slot,  c->ups,   c->stamp,   c->queued, c->lists, c->done, c->qgroup, c->glists,
-                    c->ctrl,  c->err_flag, c->log, c->scratch, c->fstage, c->d_mlp};
+                    c->ctrl,  c->log, c->scratch, c->fstage, c->d_mlp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_err) cudaFreeHost(c->h_err);
@@ -275,7 +274,6 @@ eik_status eik_create(eik_ctx** out, const int32_t dims[3], double h, const void
         {reinterpret_cast<void**>(&c->qgroup), eikg::kRing * static_cast<size_t>(c->ngroups) * sizeof(int32_t)},
         {reinterpret_cast<void**>(&c->glists), eikg::kRing * static_cast<size_t>(c->ngroups) * sizeof(int32_t)},
         {reinterpret_cast<void**>(&c->ctrl), sizeof(eikg::Ctrl)},
-        {reinterpret_cast<void**>(&c->err_flag), sizeof(int)},
     };
     for (auto& a : allocs) {
         e = dalloc(a.p, a.bytes);

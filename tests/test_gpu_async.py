@@ -104,3 +104,23 @@ def test_async_result_to_device_and_deferred_speed_errors(eik):
         assert np.array_equal(out.cpu().numpy(), ref)
     finally:
         eik.eik_destroy(ctx)
+
+
+def test_sync_with_a_solve_in_flight(eik):
+    """eik_sync waits for a queued solve; its statistics still come from eik_wait, once."""
+    w = synth.workload("C2", 48)
+    F = np.ascontiguousarray(w.speed(), dtype=np.float32)
+    ctx = eik.eik_create(w.dims, w.h, F, "fp32")
+    try:
+        eik.eik_add_sources(ctx, w.sources)
+        eik.eik_solve_async(ctx, 2 * w.h)
+        eik.eik_sync(ctx)
+        st = eik.eik_wait(ctx)
+        assert st["restarts"] > 0 and st["status"] == 0
+        with pytest.raises(eik.EikError, match="no solve in flight"):
+            eik.eik_wait(ctx)
+        out = np.empty_like(F)
+        eik.eik_result(ctx, out)
+        assert np.array_equal(out, blocking(eik, w, F, 2 * w.h))
+    finally:
+        eik.eik_destroy(ctx)
