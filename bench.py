@@ -33,10 +33,13 @@ if ROOT not in sys.path:
 METRIC = "Eikonal Mpoints/s at 512^3/1024^3 + HBM roofline %; learned vs fixed stride"
 ALGO_BYTES_PER_POINT = {"fp32": 8, "fp64": 16}      # read F once + write psi once
 KERNELS_PER_SOLVE = 4                                # gather_r, init_sources, restart_loop, restore_r
-# DRAM bytes of one k_restart_loop launch on the 1024^3 workload (fixed stride 2h, 8^3 blocks, FP32) from a
-# one-pass ncu capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum = 93.12 GB + 53.34 GB),
-# per node; profiles/launches_c4_1024_fixed2h.md gives the command.
+# DRAM bytes and warp instructions of one k_restart_loop launch on the 1024^3 workload (fixed stride 2h, 8^3
+# blocks, FP32) from a one-pass ncu capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum =
+# 93.10 GB + 53.34 GB; smsp__inst_executed.sum = 167.19 G), per node; profiles/launches_c4_1024_fixed2h.md
+# gives the commands.
 NCU_TRAFFIC_PER_NODE = {"fp32": (93.10e9 + 53.34e9) / 1024 ** 3}
+NCU_INST_PER_NODE = {"fp32": 167.19e9 / 1024 ** 3}
+ISSUE_PER_SM_CYCLE = 4          # warp schedulers per SM, one warp instruction per cycle each
 
 
 def measured_peaks():
@@ -455,6 +458,17 @@ def run_ours(args):
     if not args.no_batch and rank == 0:
         batch = batch_bench(eik, synth, args.batch_steps, 3, args.tune_rounds, dev)
     clocks = clk.summary()
+    # the bound the kernel actually meets: instruction issue (warp instructions per launch from the ncu
+    # capture over the launch time, against every scheduler issuing every cycle at the sampled SM clock)
+    inst = NCU_INST_PER_NODE.get(prec)
+    if inst is not None and roof is not None:
+        mhz = (clocks or {}).get("sm_mhz") or 2070.0
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        ach = inst * w.npoints / (roof["launch_ms"] * 1e-3)
+        pk = sms * ISSUE_PER_SM_CYCLE * mhz * 1e6
+        roof["issue"] = {"achieved": ach, "peak": pk, "unit": "warp instructions/s", "frac": ach / pk,
+                         "inst_per_node": inst, "sms": sms, "sm_mhz": mhz,
+                         "source": "ncu smsp__inst_executed.sum, one-pass capture of a full 1024^3 launch (fixed 2h)"}
     s0 = stats[-1]
     line = {"metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
