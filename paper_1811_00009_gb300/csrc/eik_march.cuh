@@ -57,10 +57,22 @@ __device__ __forceinline__ double from_bits(unsigned long long u) {
 }
 __device__ __forceinline__ float vabs(float v) { return fabsf(v); }
 __device__ __forceinline__ double vabs(double v) { return fabs(v); }
+// Min, max and order of values that are >= 0 or +inf (every use in the march):
+// single precision on the FP32 units; double precision as integer operations on
+// the bit patterns, which order like such values, keeping them off this part's
+// narrow FP64 pipe.
 __device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
-__device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ double vmin(double a, double b) {
+    const unsigned long long x = ubits(a), y = ubits(b);
+    return from_bits(x < y ? x : y);
+}
 __device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
-__device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ double vmax(double a, double b) {
+    const unsigned long long x = ubits(a), y = ubits(b);
+    return from_bits(x > y ? x : y);
+}
+__device__ __forceinline__ bool vlt(float a, float b) { return a < b; }
+__device__ __forceinline__ bool vlt(double a, double b) { return ubits(a) < ubits(b); }
 
 __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;
@@ -97,17 +109,20 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 // The root never falls below the largest admitted value (causality of the
 // upwind scheme; exact arithmetic guarantees it, rounding could break it by an
 // ulp and let two nodes lower each other forever), hence the fmax clamps.
+// (D clamped at 0 by its sign bit, and the division by 3 as a product: the
+// FP64 pipe of this part is narrow, so only the root's own arithmetic uses it)
+__device__ __forceinline__ double clamp0(double D) { return (ubits(D) >> 63) ? 0.0 : D; }
 __device__ __forceinline__ double upwind_root(double a, double b, double c, double r) {
     double x = a + r;
-    if (!(x > b)) return x;
+    if (!vlt(b, x)) return x;
     const double d = b - a;
     const double r2 = r * r;
     double D = 2.0 * r2 - d * d;
-    x = fmax(a + (d + sqrt(fmax(D, 0.0))) * 0.5, b);
-    if (!(x > c)) return x;
+    x = vmax(a + (d + sqrt(clamp0(D))) * 0.5, b);
+    if (!vlt(c, x)) return x;
     const double e = c - a, g = c - b;
     D = 3.0 * r2 - (d * d + e * e + g * g);
-    return fmax(a + (d + e + sqrt(fmax(D, 0.0))) / 3.0, c);
+    return vmax(a + (d + e + sqrt(clamp0(D))) * (1.0 / 3.0), c);
 }
 
 // FP32: sqrt(D) as D * rsqrt(D) (the hardware reciprocal square root, a few
@@ -579,9 +594,9 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
                 T a0 = vmin(lo, mz);
                 T t1 = vmax(lo, mz);
                 T a1 = vmin(hi, t1), a2 = vmax(hi, t1);
-                if (a0 < INF) {
+                if (vlt(a0, INF)) {
                     xn = RootOf<T>::go(a0, a1, a2, S.r[q], tau, acc.fallbacks);
-                    imp = xn < c;
+                    imp = vlt(xn, c);
                 }
             }
             __syncwarp();
@@ -645,7 +660,7 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
                 if (i < n) {
                     hh = S.band[i];
                     const T v = vabs(S.psi[hh]);
-                    if (v <= thr) {
+                    if (!vlt(thr, v)) {
                         take = true;
                         S.psi[hh] = v;
                     } else {
@@ -753,7 +768,7 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
                     hh2 = S.band[base + 32 + lane];
                     v2 = vabs(S.psi[hh2]);
                 }
-                const bool take = valid && v <= thr;
+                const bool take = valid && !vlt(thr, v);
                 const bool keep = valid && !take;
                 if (take) {
                     S.psi[hh] = v;
