@@ -323,8 +323,8 @@ def test_full_size_local_equation_on_samples(eik, orc, cfg, n):
     """The full-size workloads in the configuration the benchmark times (FP32, learned schedule, 8^3
     blocks): the oracle cannot solve them, but every reachable non-source node of the discrete solution
     equals the upwind update of its neighbours (Eqs. (2.1)-(2.2)).  At 20,000 sampled nodes the GPU value
-    and the FP64 update of its six GPU neighbours agree to 32 ulps of FP32 (the FP32 root's own rounding),
-    far inside the 1e-5 x max psi bar."""
+    and the FP64 update of its six GPU neighbours agree to 8 ulps of FP32 (the FP32 root's own rounding;
+    about one ulp is seen), far inside the 1e-5 x max psi bar."""
     import torch
     from paper_1811_00009_gb300.train_schedule import load_weights
     w = synth.workload(cfg, n)
@@ -344,4 +344,4 @@ def test_full_size_local_equation_on_samples(eik, orc, cfg, n):
     gap, m = sampled_local_check(orc, w, psi, F, 20000, 1811 + n)
     print(f"{cfg} {n}^3: largest relative gap to the local update {gap:.3e} over {m} nodes")
     assert m > 19000
-    assert gap <= 32 * 2.0 ** -24, gap
+    assert gap <= 8 * 2.0 ** -24, gap
