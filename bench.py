@@ -410,7 +410,7 @@ def run_ours(args):
         ctxs = [ctx1, ctx2]
         torch.cuda.synchronize()
 
-        def pipeline(steps):
+        def pipeline(steps, marks):
             eik.eik_set_speed_async(ctxs[0], Fh.numpy(), prec)
             eik.eik_solve_async(ctxs[0], stride, **kw)
             for i in range(steps):
@@ -418,23 +418,30 @@ def run_ours(args):
                 if i + 1 < steps:
                     eik.eik_set_speed_async(nxt, Fh.numpy(), prec)
                 eik.eik_wait(cur)
+                marks.append(time.perf_counter())
                 eik.eik_result_async(cur, outs[i % 2].numpy())
                 if i + 1 < steps:
                     eik.eik_solve_async(nxt, stride, **kw)
             for c in ctxs:
                 eik.eik_sync(c)
 
-        pipeline(2)
+        pipeline(2, [])
+        marks = []
         t0 = time.perf_counter()
-        pipeline(args.e2e_steps)
+        pipeline(args.e2e_steps, marks)
         torch.cuda.synchronize()
-        e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
+        t1 = time.perf_counter()
+        e2e_s = max_over_ranks(t1 - t0, dev)
+        gaps = np.diff(np.array(marks)) * 1e3
         for c in ctxs:
             eik.eik_destroy(c)
         nb = Fd.element_size() * w.npoints
         e2e = {"value": job_rate(w.npoints, args.e2e_steps, ws, e2e_s), "unit": "Mpoints/s",
                "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb, "steps": args.e2e_steps,
-               "pipeline": "two contexts on two streams: host copies of one overlap the other's solve"}
+               "pipeline": "two contexts on two streams: host copies of one overlap the other's solve",
+               "first_solve_ms": (marks[0] - t0) * 1e3 if marks else None,
+               "step_ms_median": float(np.median(gaps)) if len(gaps) else None,
+               "last_copy_ms": (t1 - marks[-1]) * 1e3 if marks else None}
 
     # accuracy of this run's path against the FP64 oracle on the CPU-baseline sample
     err = None

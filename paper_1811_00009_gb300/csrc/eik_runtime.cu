@@ -689,7 +689,7 @@ eik_status eik_sync(eik_ctx* c) {
 
 void eik_destroy(eik_ctx* c) {
     if (!c) return;
-    if (c->in_flight) cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(c->stream);     // a solve or an asynchronous copy may still use the buffers
     free_all(c);
     delete c;
 }
