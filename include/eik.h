@@ -218,7 +218,8 @@ eik_status eik_result_async(eik_ctx *ctx, void *psi_out, int out_on_device);
  */
 eik_status eik_sync(eik_ctx *ctx);
 
-/* eik_destroy -- free the context and everything it allocated (NULL is a no-op). */
+/* eik_destroy -- wait for the work queued on the context's stream, then free the context and
+ * everything it allocated (NULL is a no-op). */
 void eik_destroy(eik_ctx *ctx);
 
 /* eik_last_error -- message of the last failure on ctx (or of the last failed
