@@ -1084,7 +1084,7 @@ eik_status eik_batch_size(const eik_batch* b, int32_t* n, int64_t* nbricks, int3
 
 void eik_batch_destroy(eik_batch* b) {
     if (!b) return;
-    if (b->in_flight) cudaStreamSynchronize(b->stream);
+    cudaStreamSynchronize(b->stream);     // nothing queued may outlive the buffers
     bfree_all(b);
     delete b;
 }
