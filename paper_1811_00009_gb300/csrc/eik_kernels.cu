@@ -388,25 +388,30 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P
 template <typename T>
 __global__ void k_layout_speed(const T* __restrict__ F, T* __restrict__ rr, int nx, int ny, int nz, int BX,
                                int BY, int64_t nbricks, double h, int* err, int seq) {
-    const int64_t total = nbricks * kBrick;
     const T INF = Num<T>::inf();
     // h/F in the working precision: one IEEE division in FP32 mode (a double
     // division per node would make this copy kernel FP64-bound on this part)
     const T hT = static_cast<T>(h);
+    // one block per row (k, j) of the padded brick grid at a time, its threads
+    // along x: each warp reads 128 contiguous bytes of F and writes 32-byte runs
+    // of four bricks; padding nodes get +inf
+    const int px = BX * 8, py = BY * 8;
+    const int64_t rows = (nbricks / (static_cast<int64_t>(BX) * BY)) * 8 * py;
     int bad = 0;
-    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
-         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int b = static_cast<int>(t >> 9);                 // brick indices fit in 32 bits
-        const int p = static_cast<int>(t & 511);
-        const int bx = b % BX, byz = b / BX, by = byz % BY, bz = byz / BY;
-        const int i = bx * 8 + (p & 7), j = by * 8 + ((p >> 3) & 7), k = bz * 8 + (p >> 6);
-        T r = INF;
-        if (i < nx && j < ny && k < nz) {
-            const T f = __ldg(F + (static_cast<int64_t>(k) * ny + j) * nx + i);
-            if (!(f >= 0) || !(f < INF)) bad = 1;
-            else if (f > 0) r = hT / f;
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int k = static_cast<int>(r / py), j = static_cast<int>(r - static_cast<int64_t>(k) * py);
+        const bool inrow = j < ny && k < nz;
+        const int64_t frow = inrow ? (static_cast<int64_t>(k) * ny + j) * nx : 0;
+        T* out = rr + ((static_cast<int64_t>(k >> 3) * BY + (j >> 3)) * BX) * kBrick + ((k & 7) * 8 + (j & 7)) * 8;
+        for (int i = threadIdx.x; i < px; i += blockDim.x) {
+            T v = INF;
+            if (inrow && i < nx) {
+                const T f = __ldg(F + frow + i);
+                if (!(f >= 0) || !(f < INF)) bad = 1;
+                else if (f > 0) v = hT / f;
+            }
+            __stcs(out + (i >> 3) * kBrick + (i & 7), v);
         }
-        __stcs(rr + t, r);
     }
     if (bad) *reinterpret_cast<volatile int*>(err) = seq;     // this upload's number marks a bad F
 }
@@ -496,9 +501,9 @@ __global__ void k_result(const T* __restrict__ slot, const unsigned long long* _
 template <typename T>
 cudaError_t launch_layout_speed(const T* F, T* rr, int nx, int ny, int nz, int BX, int BY, int64_t nbricks,
                                 double h, int* err, int seq, cudaStream_t s) {
-    const int64_t total = nbricks * kBrick;
-    int grid = static_cast<int>((total + 255) / 256);
-    if (grid > 65535 * 4) grid = 65535 * 4;
+    const int64_t rows = (nbricks / (static_cast<int64_t>(BX) * BY)) * 8 * (static_cast<int64_t>(BY) * 8);
+    int grid = static_cast<int>(rows < 65535 * 4 ? rows : 65535 * 4);
+    if (grid < 1) grid = 1;
     k_layout_speed<T><<<grid, 256, 0, s>>>(F, rr, nx, ny, nz, BX, BY, nbricks, h, err, seq);
     return cudaGetLastError();
 }
