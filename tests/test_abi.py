@@ -65,6 +65,10 @@ def test_null_context_calls_fail_cleanly(eik):
     assert L.eik_solve(None, 1.0, 8, None) == eik.EIK_EINVAL
     assert L.eik_result(None, None, 0) == eik.EIK_EINVAL
     assert L.eik_add_sources(None, 0, None) == eik.EIK_EINVAL
+    assert L.eik_set_speed_async(None, None, 0) == eik.EIK_EINVAL
+    assert L.eik_result_async(None, None, 0) == eik.EIK_EINVAL
+    assert L.eik_sync(None) == eik.EIK_EINVAL
+    assert L.eik_wait(None, None) == eik.EIK_EINVAL
     L.eik_destroy(None)
 
 
