@@ -367,6 +367,7 @@ template <typename T, bool GROUP>
 __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int warp, int32_t b, unsigned gmask,
                       int k, T bprev, T bound, bool grow, T window, int lane, MarchAcc& acc, bool publish) {
     __shared__ T s_wmin[kWarps];
+    __shared__ T s_bmin[2][kWarps];            // group rounds: band minima, by round parity
     WarpSmem<T>& S = SW[warp];
     const T INF = Num<T>::inf();
     const bool present = b >= 0;
@@ -636,13 +637,15 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
             T lmin = INF;
             for (int i = lane; i < n; i += 32) lmin = vmin(lmin, vabs(S.psi[S.band[i]]));
             T mn = warp_min_nn(lmin);
-            if (lane == 0) s_wmin[warp] = mn;
+            // (two buffers by round parity: the barriers later in the round order
+            // these reads before the writes two rounds on, so one barrier suffices)
+            T* bm = s_bmin[rounds & 1];
+            if (lane == 0) bm[warp] = mn;
             __syncthreads();
-            T g = s_wmin[0];
+            T g = bm[0];
 #pragma unroll
-            for (int i = 1; i < kWarps; ++i) g = vmin(g, s_wmin[i]);
+            for (int i = 1; i < kWarps; ++i) g = vmin(g, bm[i]);
             mn = g;
-            __syncthreads();
             if (!(mn < INF) || !(mn <= bound)) break;   // band empty, or its minimum above the bound
             if (++rounds > kRoundCap) {
                 atomicOr(&P.ctrl->status, kStRoundCap);
