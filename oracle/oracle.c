@@ -14,7 +14,7 @@
  * Sec. 2.1 with the unified heap of Sec. 2.2 (Algs. 1-4 with one block and an
  * infinite bound).  orc_block_fmm is the paper's method, Alg. 6 with Algs. 1-5.
  *
- * Readings of the paper that this file takes (listed in the design doc):
+ * Readings of the paper that this file takes:
  *  - point sources: the nodes of the cell containing a source are "on or
  *    adjacent to Gamma" (Alg. 1), psi0 = distance / F at that node;
  *  - Alg. 3's quadratic a*x^2 - 2*b*x + c = 0 is evaluated on values

@@ -5,7 +5,7 @@ method's arithmetic: it only produces the speed function F on a node-centred
 uniform grid and the physical coordinates of point sources (the data of the
 boundary value problem |grad psi| F = 1, psi = 0 on Gamma, Sec. 1 Eq. (1.1)).
 
-Grid convention (one reading of Sec. 2.1 / Sec. 3.1, see DESIGN.md): node
+Grid convention (one reading of Sec. 2.1 / Sec. 3.1): node
 (i, j, k) sits at x = (i*h, j*h, k*h); arrays have shape (nz, ny, nx) with x
 fastest; the unit cube has h = 1/(n-1).
 
