@@ -715,8 +715,9 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
             __syncwarp();
             acc.solves += total;
             solve_list(total);
-            __syncthreads();
-            refresh_internal();
+            // no barrier or refresh here: the next round's first barrier orders these
+            // writes before any other warp's marks and reads, and the ghost layer is
+            // refreshed after the next accept pass, before any solve reads it
         }
     } else {
         // Halo bit vectors, one 32-bit word per lane (bit j of lane L's word is
