@@ -35,10 +35,10 @@ ALGO_BYTES_PER_POINT = {"fp32": 8, "fp64": 16}      # read F once + write psi on
 KERNELS_PER_SOLVE = 4                                # gather_r, init_sources, restart_loop, restore_r
 # DRAM bytes and warp instructions of one k_restart_loop launch on the 1024^3 workload (fixed stride 2h, 8^3
 # blocks, FP32) from a one-pass ncu capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum =
-# 93.09 GB + 53.35 GB; smsp__inst_executed.sum = 167.56 G), per node; profiles/launches_c4_1024_fixed2h.md
+# 93.07 GB + 53.32 GB; smsp__inst_executed.sum = 168.03 G), per node; profiles/launches_c4_1024_fixed2h.md
 # gives the commands.
-NCU_TRAFFIC_PER_NODE = {"fp32": (93.09e9 + 53.35e9) / 1024 ** 3}
-NCU_INST_PER_NODE = {"fp32": 167.56e9 / 1024 ** 3}
+NCU_TRAFFIC_PER_NODE = {"fp32": (93.07e9 + 53.32e9) / 1024 ** 3}
+NCU_INST_PER_NODE = {"fp32": 168.03e9 / 1024 ** 3}
 ISSUE_PER_SM_CYCLE = 4          # warp schedulers per SM, one warp instruction per cycle each
 
 
