@@ -88,6 +88,21 @@ eik_status eik_set_speed(eik_ctx *ctx, const void *F, int F_on_device);
 eik_status eik_set_speed_async(eik_ctx *ctx, const void *F, int F_on_device);
 
 /*
+ * eik_source_nodes -- the fixed nodes (Alg. 1) a solve of this grid, speed
+ * function and sources starts from, computed on the host with the same code
+ * and the same rounding of h/F as eik_solve (no device needed).
+ *   F, precision  as in eik_create; F must be host memory here.
+ *   idx_out       linear indices (k*ny + j)*nx + i (nullable), ordered by brick
+ *                 and node within the brick; psi0_out their psi0 (nullable).
+ *   cap           capacity of the outputs; *n_out gets the count even when
+ *                 it exceeds cap (then EIK_EINVAL and nothing is written).
+ * Errors: EIK_EINVAL (bad dims, h, precision, F, or a source outside the grid).
+ */
+eik_status eik_source_nodes(const int32_t dims[3], double h, const void *F, eik_precision precision,
+                            int32_t nsrc, const double *xyz, int64_t *idx_out, double *psi0_out, int64_t cap,
+                            int64_t *n_out);
+
+/*
  * eik_add_sources -- add point sources (Gamma of Eq. (1.1)).
  *   xyz  n*3 physical coordinates (x, y, z), origin at node 0, each within
  *        [0, (n_axis - 1)*h].  The nodes of the grid cell containing a source

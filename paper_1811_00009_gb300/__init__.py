@@ -105,6 +105,10 @@ def lib():
             L.eik_create.argtypes = [C.POINTER(vp), C.POINTER(i32), dbl, vp, C.c_int, C.c_int, vp]
             L.eik_set_speed.restype = i32
             L.eik_set_speed.argtypes = [vp, vp, C.c_int]
+            L.eik_source_nodes.restype = i32
+            L.eik_source_nodes.argtypes = [C.POINTER(i32), dbl, vp, C.c_int, i32, C.POINTER(C.c_double),
+                                           C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int64,
+                                           C.POINTER(C.c_int64)]
             L.eik_set_speed_async.restype = i32
             L.eik_set_speed_async.argtypes = [vp, vp, C.c_int]
             L.eik_result_async.restype = i32
@@ -251,6 +255,23 @@ def eik_set_speed_async(ctx, F, precision="fp32"):
     ptr, on_dev, keep = _buffer(F, np.float32 if _precision(precision) == EIK_FP32 else np.float64)
     _check(lib().eik_set_speed_async(ctx, ptr, on_dev), ctx)
     return keep
+
+
+def eik_source_nodes(dims, h, F, sources, precision="fp32"):
+    """(linear indices, psi0) of the fixed nodes a solve would start from (host computation, Alg. 1)."""
+    prec = _precision(precision)
+    arr = np.ascontiguousarray(np.asarray(F, dtype=np.float32 if prec == EIK_FP32 else np.float64))
+    xyz = np.ascontiguousarray(np.asarray(sources, dtype=np.float64).reshape(-1, 3))
+    d = (C.c_int32 * 3)(*[int(x) for x in dims])
+    n = C.c_int64()
+    cap = 8 * max(1, len(xyz))
+    idx = np.zeros(cap, np.int64)
+    val = np.zeros(cap, np.float64)
+    st = lib().eik_source_nodes(d, float(h), C.c_void_p(arr.ctypes.data), prec, len(xyz),
+                                xyz.ctypes.data_as(C.POINTER(C.c_double)), idx.ctypes.data_as(C.POINTER(C.c_int64)),
+                                val.ctypes.data_as(C.POINTER(C.c_double)), cap, C.byref(n))
+    _check(st, None)
+    return idx[:n.value].copy(), val[:n.value].copy()
 
 
 def eik_add_sources(ctx, xyz) -> None:

@@ -334,6 +334,61 @@ eik_status eik_set_speed_async(eik_ctx* c, const void* F, int F_on_device) {
     return upload_speed(c, F, F_on_device, false);
 }
 
+eik_status eik_source_nodes(const int32_t dims[3], double h, const void* F, eik_precision precision, int32_t nsrc,
+                            const double* xyz, int64_t* idx_out, double* psi0_out, int64_t cap, int64_t* n_out) {
+    if (!dims || !F || !n_out || (nsrc > 0 && !xyz) || nsrc < 0)
+        return fail(nullptr, EIK_EINVAL, "eik_source_nodes: NULL argument or nsrc < 0");
+    if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1 || !finite_pos(h))
+        return fail(nullptr, EIK_EINVAL, "eik_source_nodes: bad dims or h");
+    if (precision != EIK_FP32 && precision != EIK_FP64)
+        return fail(nullptr, EIK_EINVAL, "eik_source_nodes: bad precision");
+    const int nx = dims[0], ny = dims[1], nz = dims[2];
+    const int dd[3] = {nx, ny, nz};
+    for (int s = 0; s < nsrc; ++s)
+        for (int a = 0; a < 3; ++a) {
+            const double v = xyz[3 * s + a];
+            if (!std::isfinite(v) || v < -1e-9 * h || v > (dd[a] - 1) * h + 1e-9 * h)
+                return fail(nullptr, EIK_EINVAL, "eik_source_nodes: source " + std::to_string(s) + " lies outside the grid");
+        }
+    // the candidates and their h/F as a solve sees them (h/F rounded as the speed re-layout rounds it)
+    const eikh::Bricks geo{(nx + 7) / 8, (ny + 7) / 8, (nz + 7) / 8, 0};
+    std::vector<eikh::Cand> cand;
+    eikh::source_candidates(xyz, nsrc, nx, ny, nz, h, geo, cand);
+    std::vector<double> r(cand.size());
+    auto lin = [&](const eikh::Cand& c, int* i, int* j, int* k) {
+        const int bx = c.b % geo.BX, by = (c.b / geo.BX) % geo.BY, bz = c.b / (geo.BX * geo.BY);
+        *i = bx * 8 + (c.p & 7);
+        *j = by * 8 + ((c.p >> 3) & 7);
+        *k = bz * 8 + (c.p >> 6);
+    };
+    for (size_t t = 0; t < cand.size(); ++t) {
+        int i, j, k;
+        lin(cand[t], &i, &j, &k);
+        const int64_t q = (static_cast<int64_t>(k) * ny + j) * nx + i;
+        double rv = INFINITY;
+        if (precision == EIK_FP32) {
+            const float f = static_cast<const float*>(F)[q];
+            if (!(f >= 0.0f) || !std::isfinite(f)) return fail(nullptr, EIK_EINVAL, "F must be finite and >= 0");
+            if (f > 0.0f) rv = static_cast<double>(static_cast<float>(h) / f);
+        } else {
+            const double f = static_cast<const double*>(F)[q];
+            if (!(f >= 0.0) || !std::isfinite(f)) return fail(nullptr, EIK_EINVAL, "F must be finite and >= 0");
+            if (f > 0.0) rv = h / f;
+        }
+        r[t] = rv;
+    }
+    const std::vector<eikh::FixNode> uf = eikh::fixed_nodes(cand, r, h);
+    *n_out = static_cast<int64_t>(uf.size());
+    if (static_cast<int64_t>(uf.size()) > cap) return fail(nullptr, EIK_EINVAL, "eik_source_nodes: cap too small");
+    for (size_t t = 0; t < uf.size(); ++t) {
+        int i, j, k;
+        lin(eikh::Cand{uf[t].b, uf[t].p, 0.0}, &i, &j, &k);
+        if (idx_out) idx_out[t] = (static_cast<int64_t>(k) * ny + j) * nx + i;
+        if (psi0_out) psi0_out[t] = uf[t].v;
+    }
+    return EIK_OK;
+}
+
 eik_status eik_add_sources(eik_ctx* c, int32_t n, const double* xyz) {
     if (!c) return fail(nullptr, EIK_EINVAL, "eik_add_sources: ctx is NULL");
     if (c->in_flight) return fail(c, EIK_ESTATE, "eik_add_sources: a solve is in flight (call eik_wait)");

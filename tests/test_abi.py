@@ -103,3 +103,42 @@ def test_batch_create_rejects_bad_items_before_touching_the_device(eik, case):
     assert not out.value
     msg = L.eik_batch_last_error(None).decode()
     assert msg and (case == "n0" or "item 1" in msg)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_source_nodes_match_the_oracle(eik, orc, precision):
+    """The fixed nodes of Alg. 1 (reading: the nodes of each source's cell, psi0 = distance / F, the
+    smallest over sources, none on a barrier node unless the source sits on it), as the solve computes
+    them on the host, against the oracle's: same nodes; psi0 equal up to the rounding of h/F (FP32: h and
+    h/F rounded to single precision, a few 1e-7 relative)."""
+    import synth
+    u = synth.uniform(77, 1, 4000)
+    tol = 4e-7 if precision == "fp32" else 4e-16
+    dt = np.float32 if precision == "fp32" else np.float64
+    for trial in range(20):
+        v = u[trial * 40:(trial + 1) * 40]
+        dims = (1 + int(v[0] * 20), 1 + int(v[1] * 20), 1 + int(v[2] * 20))
+        h = 0.01 + v[3]
+        F = (0.3 + 2.0 * synth.uniform(100 + trial, 1, dims[0] * dims[1] * dims[2])).reshape(dims[::-1])
+        F[synth.uniform(200 + trial, 1, F.size).reshape(F.shape) < 0.2] = 0.0        # barrier nodes
+        F = F.astype(dt)
+        ns = 1 + int(v[4] * 4)
+        src = []
+        for s in range(ns):
+            p = []
+            for a in range(3):
+                ext = (dims[a] - 1) * h
+                w = v[5 + 3 * s + a]
+                # on a node, on a cell edge or face, or inside a cell
+                p.append(min(ext, round(w * (dims[a] - 1)) * h) if w < 0.3 else w * ext)
+            src.append(p)
+        src = np.array(src)
+        idx, val = eik.eik_source_nodes(dims, h, F, src, precision)
+        ridx, rval = orc.fix_nodes(F.astype(np.float64), h, src)
+        o, ro = np.argsort(idx), np.argsort(ridx)
+        assert np.array_equal(idx[o], ridx[ro]), trial
+        if len(val):
+            den = np.where(rval[ro] > 0, rval[ro], 1.0)
+            assert np.all(np.abs(val[o] - rval[ro]) <= tol * den), trial
+    with pytest.raises(eik.EikError, match="outside"):
+        eik.eik_source_nodes((4, 4, 4), 0.1, np.ones((4, 4, 4), dt), [[0.0, 0.0, 0.5]], precision)
