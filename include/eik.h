@@ -145,6 +145,9 @@ typedef struct {
     double width;           /* width_band of Alg. 6 (0 = +inf: the full solve).  A finite width caps the
                                bound: psi is exact at every node with psi <= width; a node above it keeps a
                                tentative value >= its exact one, or +inf */
+    int64_t wait_polls;     /* polls (of 32 ns - 4 us naps) before a device-side wait gives up and the solve
+                               ends with EIK_ETIMEOUT (0 = default 2^22, seconds).  Small values let a
+                               test make the waits run out; the context stays usable */
 } eik_params;
 
 /* Per-solve statistics, filled by eik_solve / eik_wait. */

@@ -45,7 +45,7 @@ class eik_params(C.Structure):
     _fields_ = [("stride", C.c_double), ("block_dim", C.c_int32), ("schedule", C.c_int32),
                 ("window", C.c_double), ("fallback_tau", C.c_double), ("max_restarts", C.c_int64),
                 ("log_restarts", C.c_int32), ("seed", C.c_int32), ("loop_events", C.c_void_p * 2),
-                ("switch_margin", C.c_double), ("width", C.c_double)]
+                ("switch_margin", C.c_double), ("width", C.c_double), ("wait_polls", C.c_int64)]
 
 
 class eik_stats(C.Structure):

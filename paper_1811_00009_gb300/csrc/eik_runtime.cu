@@ -577,7 +577,7 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
         L.fallback_tau = P.fallback_tau;
         L.max_restarts = P.max_restarts;
         L.width = P.width;
-        L.wait_limit = eikg::kWaitPolls;
+        L.wait_limit = P.wait_polls > 0 ? P.wait_polls : eikg::kWaitPolls;
         L.sched = P.schedule;
         L.mlp = (P.schedule == EIK_SCHED_LEARNED) ? c->d_mlp : nullptr;
         L.h = c->h;
@@ -608,6 +608,7 @@ eik_status check_params(eik_ctx* c, const eik_params* p) {
         return fail(c, EIK_EINVAL, "fallback_tau must lie in [0, 1]");
     if (p->max_restarts < 0) return fail(c, EIK_EINVAL, "max_restarts must be >= 0");
     if (!(p->width >= 0.0)) return fail(c, EIK_EINVAL, "width must be >= 0 (0 = +inf)");
+    if (p->wait_polls < 0) return fail(c, EIK_EINVAL, "wait_polls must be >= 0 (0 = default)");
     return EIK_OK;
 }
 

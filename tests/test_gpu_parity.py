@@ -345,3 +345,28 @@ def test_full_size_local_equation_on_samples(eik, orc, cfg, n):
     print(f"{cfg} {n}^3: largest relative gap to the local update {gap:.3e} over {m} nodes")
     assert m > 19000
     assert gap <= 8 * 2.0 ** -24, gap
+
+
+def test_device_waits_give_up_and_the_context_stays_usable(eik, orc):
+    """Failure detection without a GPU fault: with a limit of one poll, the device-side waits (the grid
+    barrier, a neighbour's march, a work-list entry) run out; the kernel records it, every warp returns,
+    the solve reports EIK_ETIMEOUT, and the next solve on the same context is correct.  (8^3 blocks only:
+    that path has no CTA-wide barrier that a returning warp could leave waiting.)"""
+    w = synth.workload("C2", 96)
+    F = w.speed()
+    Fh = np.ascontiguousarray(F.astype(np.float32))
+    ctx = eik.eik_create(w.dims, w.h, Fh, "fp32")
+    try:
+        eik.eik_add_sources(ctx, w.sources)
+        with pytest.raises(eik.EikError) as e:
+            eik.eik_solve_ex(ctx, w.h, block_dim=8, wait_polls=1)
+        assert e.value.status == eik.EIK_ETIMEOUT
+        assert "wait limit" in str(e.value)
+        with pytest.raises(eik.EikError, match="no successful solve"):
+            eik.eik_result(ctx, np.empty_like(Fh))
+        eik.eik_solve_ex(ctx, 2 * w.h, block_dim=8)
+        psi = np.empty_like(Fh)
+        eik.eik_result(ctx, psi)
+    finally:
+        eik.eik_destroy(ctx)
+    assert_parity(psi.astype(np.float64), orc.fmm(F.astype(np.float32).astype(np.float64), w.h, w.sources), "fp32")
