@@ -44,6 +44,9 @@ def test_host_only_entry_points(eik):
     assert "sm_103a" in eik.eik_version()
     p = eik.eik_params_default()
     assert p.block_dim == 8 and p.window == 2.0 and p.fallback_tau == 0.125
+    # the later fields too: a layout mismatch between eik.h and the binding would garble them
+    assert p.max_restarts == 1 << 24 and p.switch_margin == 0.02 and p.width == 0.0 and p.wait_polls == 0
+    assert C.sizeof(eik.eik_params) % 8 == 0
 
 
 @pytest.mark.parametrize("dims,h", [((0, 4, 4), 0.1), ((4, 4, -1), 0.1), ((4, 4, 4), 0.0),
