@@ -47,6 +47,9 @@ def test_host_only_entry_points(eik):
     # the later fields too: a layout mismatch between eik.h and the binding would garble them
     assert p.max_restarts == 1 << 24 and p.switch_margin == 0.02 and p.width == 0.0 and p.wait_polls == 0
     assert C.sizeof(eik.eik_params) % 8 == 0
+    bp = eik.eik_batch_params()
+    eik.lib().eik_batch_params_default(C.byref(bp))
+    assert bp.ctas_per_sm == 0 and bp.window == 2.0 and bp.fallback_tau == 0.125 and bp.max_restarts == 1 << 24
 
 
 @pytest.mark.parametrize("dims,h", [((0, 4, 4), 0.1), ((4, 4, -1), 0.1), ((4, 4, 4), 0.0),
