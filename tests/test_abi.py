@@ -148,3 +148,26 @@ def test_source_nodes_match_the_oracle(eik, orc, precision):
             assert np.all(np.abs(val[o] - rval[ro]) <= tol * den), trial
     with pytest.raises(eik.EikError, match="outside"):
         eik.eik_source_nodes((4, 4, 4), 0.1, np.ones((4, 4, 4), dt), [[0.0, 0.0, 0.5]], precision)
+
+
+def test_binding_argument_counts_match_the_header(eik):
+    """Every entry point the binding types (argtypes) takes as many arguments as eik.h declares."""
+    text = ""
+    for hdr in os.listdir(os.path.join(ROOT, "include")):
+        if hdr.endswith(".h"):
+            text += open(os.path.join(ROOT, "include", hdr)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    protos = re.findall(r"(?:eik_status|void|const\s+char\s*\*|int32_t|int64_t)\s*\**\s*(eik_\w+)\s*\(([^)]*)\)\s*;",
+                        text)
+    L = eik.lib()
+    checked = 0
+    for name, args in protos:
+        fn = getattr(L, name, None)
+        types = getattr(fn, "argtypes", None) if fn is not None else None
+        if not types:
+            continue
+        a = args.strip()
+        n = 0 if a in ("", "void") else len(a.split(","))
+        assert len(types) == n, (name, len(types), n)
+        checked += 1
+    assert checked >= 20
