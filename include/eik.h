@@ -127,9 +127,12 @@ typedef enum {
 } eik_schedule;
 
 typedef struct {
-    double stride;          /* bound increment in psi units (> 0; +inf = the naive block method) */
+    double stride;          /* bound increment in psi units (> 0; +inf = the naive block method); 0 selects
+                               the learned schedule (as schedule = EIK_SCHED_LEARNED, with 2h for restarts
+                               1-2) */
     int32_t block_dim;      /* block edge in nodes: 8 (one warp per block) or 16 (one CTA per block of
-                               2x2x2 bricks); 0 = default 8 */
+                               2x2x2 bricks); 0 = picked: by the network under the learned schedule (8 for
+                               restarts 1-2), else the edge eik_autotune chose for the context, else 8 */
     int32_t schedule;       /* eik_schedule */
     double window;          /* acceptance window factor omega: each march round accepts every band
                                point within omega * h / F_max(block) of the band minimum
@@ -187,12 +190,25 @@ typedef struct {
 void eik_params_default(eik_params *p);
 
 /*
- * eik_solve -- run the method (Alg. 6) with a fixed stride and wait for it.
- *   stride     > 0, may be +inf.
- *   block_dim  8 or 16, or 0 for the default (8).
+ * eik_solve -- run the method (Alg. 6: restarts that raise bound_band by the
+ * stride, march every active block up to it with Algs. 2-4 and exchange ghost
+ * layers with Alg. 5, until no block is active) and wait for it.
+ *   stride     > 0 (may be +inf: the naive block method of Sec. 3.4): every
+ *              restart raises the bound by it.  0: the learned schedule picks
+ *              the stride (and, with block_dim 0, the block edge) of every
+ *              restart from restart 3 on; restarts 1-2 take 2h.  The
+ *              context's network weights are used (every context starts
+ *              with the shipped ones; eik_set_schedule replaces them).
+ *   block_dim  8 or 16; 0 = picked (the network under the learned schedule,
+ *              else the edge eik_autotune chose for the context, else 8).
  *   stats      nullable.
- * Returns EIK_ESTATE if no source was added, EIK_ETIMEOUT if the restart cap
- * or a device wait limit was hit.
+ * The result does not depend on the stride, the schedule or the block edge,
+ * bit for bit (the root of Alg. 3 is evaluated as a monotone function of the
+ * neighbour values, so every order of work reaches the same fixed point).
+ * Returns EIK_ESTATE if no source was added or stride 0 is asked for after
+ * the weights were unloaded, EIK_EINVAL for a negative or NaN stride or
+ * another block edge, EIK_ETIMEOUT if the restart cap or a device wait limit
+ * was hit.
  */
 eik_status eik_solve(eik_ctx *ctx, double stride, int32_t block_dim, eik_stats *stats);
 
@@ -205,6 +221,19 @@ eik_status eik_solve_async(eik_ctx *ctx, const eik_params *params);
 eik_status eik_wait(eik_ctx *ctx, eik_stats *stats);
 
 /*
+ * eik_autotune -- pick the fixed stride and block edge of this context's
+ * grid by timing solves on the device (the paper's Secs. 3.4-3.6 study the
+ * same two parameters).  Candidates: stride c*h with c in {1, 1.5, 2, 2.5, 3,
+ * 4} and block edge 8 or 16.  Successive halving: time every candidate once,
+ * keep the best third, time the survivors twice as often, until one is left
+ * (at most `rounds` rounds; 0 = no limit).  Later solves with block_dim 0 and
+ * a fixed stride use the chosen edge.  stride_out, block_out, best_ms (its
+ * median device time) are nullable.  The context's psi afterwards is that of
+ * the last timed solve.  Errors: EIK_ESTATE (no source, or a solve in flight).
+ */
+eik_status eik_autotune(eik_ctx *ctx, int32_t rounds, double *stride_out, int32_t *block_out, double *best_ms);
+
+/*
  * eik_restart_log -- copy up to cap per-restart records of the last solve
  * (made with log_restarts set) into out (host memory); *n gets the count.
  */
@@ -212,7 +241,9 @@ eik_status eik_restart_log(eik_ctx *ctx, eik_restart_rec *out, int64_t cap, int6
 
 /*
  * eik_result -- copy psi of the last solve into psi_out (nx*ny*nz, context
- * precision, x fastest).  Unreachable nodes and barrier nodes are +inf.
+ * precision, x fastest).  This is psi_i,j,k of Sec. 2.1 on every node of the
+ * grid at the end of Alg. 6, gathered from the interiors Omega^ib of the
+ * blocks.  Unreachable nodes and barrier nodes (F = 0, Sec. 3.3) are +inf.
  * Errors: EIK_ESTATE before the first successful solve.
  */
 eik_status eik_result(eik_ctx *ctx, void *psi_out, int out_on_device);
@@ -237,11 +268,13 @@ eik_status eik_result_async(eik_ctx *ctx, void *psi_out, int out_on_device);
 eik_status eik_sync(eik_ctx *ctx);
 
 /* eik_destroy -- wait for the work queued on the context's stream, then free the context and
- * everything it allocated (NULL is a no-op). */
+ * everything it allocated: the block data of Sec. 2.3 (per-block psi, h/F, ghost layers and
+ * flags), the work lists and the control block (NULL is a no-op). */
 void eik_destroy(eik_ctx *ctx);
 
 /* eik_last_error -- message of the last failure on ctx (or of the last failed
- * eik_create when ctx is NULL).  Valid until the next call on ctx. */
+ * eik_create when ctx is NULL).  Valid until the next call on ctx.  (Error reporting has no
+ * counterpart in the paper.) */
 const char *eik_last_error(const eik_ctx *ctx);
 
 /* eik_version -- library version string. */
@@ -268,7 +301,8 @@ const char *eik_version(void);
 eik_status eik_sched_actions(double *stride_h, int32_t *block_dim, int32_t cap, int32_t *n);
 
 /* eik_set_schedule -- load network weights (host, n = EIK_SCHED_PARAMS finite floats) into the
- * context for EIK_SCHED_LEARNED; w = NULL unloads them. */
+ * context for EIK_SCHED_LEARNED; w = NULL unloads them.  A new context holds the weights shipped
+ * with the library (trained by the project on its own per-restart timings). */
 eik_status eik_set_schedule(eik_ctx *ctx, const float *w, int32_t n);
 
 /* eik_mlp_forward -- Y[B][ACTIONS] = network(X[B][INPUTS]); all DEVICE pointers; async on stream. */
@@ -411,8 +445,9 @@ const char *eik_batch_last_error(const eik_batch *b);
  *
  * No counterpart in the paper: this is a deployment entry point.  It serves
  * callers that cannot call cudaMalloc at solve time -- code that lives under
- * a memory pool or caching allocator it does not own, code that runs inside
- * a CUDA stream capture, and embedders that must keep the process's device
+ * a memory pool or caching allocator it does not own (a cudaMalloc there
+ * would take memory behind the allocator's back, or fail once the pool has
+ * reserved the device), and embedders that must keep the process's device
  * footprint fixed.  All working memory of the solve lives in one fixed device
  * array inside the library (EIK_NOALLOC_SCRATCH_BYTES, 64 MiB), which every
  * GPU that loads the library holds until the process exits.
@@ -423,12 +458,19 @@ const char *eik_batch_last_error(const eik_batch *b);
  *   F         nx*ny*nz float speeds in DEVICE memory (x fastest), finite, >= 0.
  *   nsrc, xyz 1..EIK_NOALLOC_MAX_SOURCES point sources, host memory, as in
  *             eik_add_sources.
- *   params    nullable (defaults); stride must be > 0; fixed schedule, 8^3 blocks.
+ *   params    nullable (defaults); checked as eik_solve_ex checks them, and
+ *             stride must be > 0: fixed schedule and 8^3 blocks only
+ *             (EIK_ENOTSUP otherwise, and for log_restarts, whose records
+ *             would need memory); wait_polls and loop_events are honoured.
  *   psi_out   nx*ny*nz floats in DEVICE memory: the solution (FP32 mode only).
  *   stats     nullable.
- *   stream    cudaStream_t or NULL.  The call returns after the solve finished.
+ *   stream    cudaStream_t or NULL.  The call returns after the solve finished
+ *             (it waits for the stream twice: once to read the speed check
+ *             and the h/F of the source nodes, once at the end).
  * Errors: EIK_EINVAL for a grid above the limit (with a message saying so),
- * bad arguments or bad F; eik_noalloc_last_error() describes the failure.
+ * bad arguments or bad F; EIK_ETIMEOUT when the restart cap or a device wait
+ * limit ends the solve (the next call is not affected);
+ * eik_noalloc_last_error() describes the failure.
  *
  * The array's device address is looked up on the first call made with a
  * given device current: make that first call before any stream capture.

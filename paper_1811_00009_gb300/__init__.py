@@ -129,6 +129,8 @@ def lib():
             L.eik_solve_async.argtypes = [vp, C.POINTER(eik_params)]
             L.eik_wait.restype = i32
             L.eik_wait.argtypes = [vp, C.POINTER(eik_stats)]
+            L.eik_autotune.restype = i32
+            L.eik_autotune.argtypes = [vp, i32, C.POINTER(dbl), C.POINTER(i32), C.POINTER(dbl)]
             L.eik_restart_log.restype = i32
             L.eik_restart_log.argtypes = [vp, C.POINTER(eik_restart_rec), i64, C.POINTER(i64)]
             L.eik_result.restype = i32
@@ -308,6 +310,8 @@ def _params(stride: float, **kw) -> eik_params:
 
 
 def eik_solve(ctx, stride: float, block_dim: int = 8) -> Dict[str, Any]:
+    """Solve (Alg. 6) and wait.  stride 0 selects the learned schedule; block_dim 0 lets the schedule or
+    eik_autotune pick the block edge."""
     s = eik_stats()
     _check(lib().eik_solve(ctx, float(stride), int(block_dim), C.byref(s)), ctx)
     return _stats_dict(s)
@@ -329,6 +333,13 @@ def eik_wait(ctx) -> Dict[str, Any]:
     s = eik_stats()
     _check(lib().eik_wait(ctx, C.byref(s)), ctx)
     return _stats_dict(s)
+
+
+def eik_autotune(ctx, rounds: int = 0) -> Dict[str, Any]:
+    """Time the candidate fixed strides and block edges on this context; returns the winner."""
+    stride, block, ms = C.c_double(), C.c_int32(), C.c_double()
+    _check(lib().eik_autotune(ctx, int(rounds), C.byref(stride), C.byref(block), C.byref(ms)), ctx)
+    return {"stride": stride.value, "block_dim": block.value, "ms": ms.value}
 
 
 def eik_restart_log(ctx, cap: int = 1 << 16) -> List[Dict[str, Any]]:

@@ -31,11 +31,32 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
+WEIGHTS = os.path.join(PKG, "schedule_weights.json")
+
+
 def _inputs() -> List[str]:
     files = [os.path.join(CSRC, s) for s in SOURCES]
     files += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     files.append(os.path.join(INCLUDE, "eik.h"))
+    files.append(WEIGHTS)
     return files
+
+
+def write_weights_include(bdir: str) -> None:
+    """The shipped schedule-network weights as a C array (every new context starts with them)."""
+    import json
+    with open(WEIGHTS) as fh:
+        w = json.load(fh)["weights"]
+    body = ",\n".join(", ".join(repr(float(v)) + "f" for v in w[i:i + 6]) for i in range(0, len(w), 6))
+    text = ("// Written by build.py from schedule_weights.json: the shipped weights of the\n"
+            "// restart-schedule network (EIK_SCHED_PARAMS floats).\n"
+            f"#define EIK_SCHED_DEFAULT_COUNT {len(w)}\n"
+            "static const float kSchedDefault[EIK_SCHED_DEFAULT_COUNT] = {\n" + body + "\n};\n")
+    path = os.path.join(bdir, "eik_sched_weights.inc")
+    old = open(path).read() if os.path.exists(path) else None
+    if old != text:
+        with open(path, "w") as fh:
+            fh.write(text)
 
 
 def stale() -> bool:
@@ -51,11 +72,12 @@ def build(force: bool = False, verbose_ptxas: bool = False, extra: Optional[List
     cc = nvcc()
     bdir = os.path.join(PKG, "_build")
     os.makedirs(bdir, exist_ok=True)
+    write_weights_include(bdir)
     procs = []
     objs = []
     for src in SOURCES:
         obj = os.path.join(bdir, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, "-I" + bdir, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose_ptxas:
             cmd.insert(1, "-Xptxas=-v")
         if extra:

@@ -67,7 +67,8 @@ __device__ void batch_restart_end(const LoopParams<T>& P) {
     C->head[par] = 0;
     C->gcount[par] = 0;
     C->ghead[par] = 0;
-    if (n_next == 0) {
+    if (n_next == 0 || (__ldcg(&C->status) & kStWaitTimeout)) {
+        // (no work left, or a wait somewhere ran out: no warp starts another restart)
         C->done = 1;
         C->t_end = now;
     } else if (k >= P.max_restarts) {
@@ -102,11 +103,14 @@ template <typename T>
 __global__ void __launch_bounds__(kWarps * 32, 3) k_batch_loop(LoopParams<T> P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
+    __shared__ int s_arrived;
     __shared__ LoopState s_state[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<T>* SW = reinterpret_cast<WarpSmem<T>*>(smem_raw);
     LoopState& L = s_state[warp];              // the loop's bookkeeping, kept out of registers
     Ctrl* C = P.ctrl;
+    if (threadIdx.x == 0) s_arrived = 0;
+    __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const unsigned long long t0 = globaltimer();
         C->t_begin = t0;
@@ -120,7 +124,8 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_batch_loop(LoopParams<T> P) 
         const int s = k % kRing;
         const bool early_k = P.early != 0;
         if (P.early) clear_used_slot(P, k);
-        // ---- 16^3 blocks: one CTA per group of 2x2x2 bricks
+        // ---- 16^3 blocks: one CTA per group of 2x2x2 bricks (the CTA goes on only as a whole)
+        if (!cta_go(C, true, lane, &s_arrived)) return;
         {
             const int n = __ldcg(&C->gcount[s]);
             for (;;) {
@@ -214,7 +219,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_batch_loop(LoopParams<T> P) 
                     if (!wait_ready(P, G, b, k, lane)) b = -2;
                 }
                 if (b == -2) {
-                    if (lane == 0) atomicOr(&C->status, kStWaitTimeout);
+                    give_up(C, lane);
                     return;
                 }
                 if (b < 0) {
@@ -224,9 +229,11 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_batch_loop(LoopParams<T> P) 
                         quit = ++L.polls > P.wait_limit;
                         nap = L.nap;
                         if (L.nap < 4096) L.nap <<= 1;
-                        if (quit) atomicOr(&C->status, kStWaitTimeout);
                     }
-                    if (__shfl_sync(kFull, quit, 0)) return;
+                    if (__shfl_sync(kFull, quit, 0)) {
+                        give_up(C, lane);
+                        return;
+                    }
                     __nanosleep(__shfl_sync(kFull, nap, 0));
                     continue;
                 }

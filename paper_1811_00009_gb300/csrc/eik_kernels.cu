@@ -182,7 +182,8 @@ __device__ void restart_end(const LoopParams<T>& P, int lane, float* scratch) {
     C->head[s] = 0;
     C->gcount[s] = 0;
     C->ghead[s] = 0;
-    if (n_next == 0) {
+    if (n_next == 0 || (__ldcg(&C->status) & kStWaitTimeout)) {
+        // (no work left, or a wait somewhere ran out: no warp starts another restart)
         C->done = 1;
         C->t_end = now;
     } else if (k >= P.max_restarts) {
@@ -225,11 +226,14 @@ template <typename T>
 __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
+    __shared__ int s_arrived;
     __shared__ LoopState s_state[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<T>* SW = reinterpret_cast<WarpSmem<T>*>(smem_raw);
     LoopState& L = s_state[warp];              // the loop's bookkeeping, kept out of registers
     Ctrl* C = P.ctrl;
+    if (threadIdx.x == 0) s_arrived = 0;
+    __syncthreads();
     // Work lists the marches fill: the brick list, and for fixed 16^3 blocks
     // the group list too.  Under a learned or random schedule a 16^3 restart
     // builds its group list from its brick list when it starts (such restarts
@@ -268,10 +272,10 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P
         }
         __syncwarp();
         if (mode == 16) {
-            if (!(G.lists & 2u) &&
-                !groups_from_bricks(C, P.list[s], P.qgroup + static_cast<int64_t>(s) * P.ngroups, P.glist[s], s, k,
-                                    P.BX, P.BY, P.GX, P.GY, lane, P.wait_limit))
-                return;
+            const bool ok = (G.lists & 2u) ||
+                            groups_from_bricks(C, P.list[s], P.qgroup + static_cast<int64_t>(s) * P.ngroups,
+                                               P.glist[s], s, k, P.BX, P.BY, P.GX, P.GY, lane, P.wait_limit);
+            if (!cta_go(C, ok, lane, &s_arrived)) return;
             // one CTA per group of 2x2x2 bricks
             const int n = __ldcg(&C->gcount[s]);
             for (;;) {
@@ -349,7 +353,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P
                 }
                 if (b >= 0 && !wait_ready(P, G, b, k, lane)) b = -2;
                 if (b == -2) {
-                    if (lane == 0) atomicOr(&C->status, kStWaitTimeout);
+                    give_up(C, lane);
                     return;
                 }
                 if (b < 0) {
@@ -359,9 +363,11 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P
                         quit = ++L.polls > P.wait_limit;
                         nap = L.nap;
                         if (L.nap < 4096) L.nap <<= 1;
-                        if (quit) atomicOr(&C->status, kStWaitTimeout);
                     }
-                    if (__shfl_sync(kFull, quit, 0)) return;
+                    if (__shfl_sync(kFull, quit, 0)) {
+                        give_up(C, lane);
+                        return;
+                    }
                     __nanosleep(__shfl_sync(kFull, nap, 0));
                     continue;
                 }

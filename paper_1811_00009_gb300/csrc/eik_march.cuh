@@ -98,21 +98,137 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 
 // ---------------------------------------------------------------------------
 // Alg. 3: the upwind root for sorted upwind values a <= b <= c (b, c may be
-// +inf) and r = h/F.  Alg. 3 solves a x^2 - 2 b x + c = 0 for the id
-// smallest values, growing id while the root exceeds the next value.  Here
-// the same root is written without cancellation: with k admitted values,
+// +inf) and r = h/F.  Alg. 3 solves sum_i (x - v_i)^2 = r^2 (Eq. (2.1)-(2.2))
+// for the id smallest values, growing id while the root exceeds the next
+// value.  Equivalently the root is the x with G(x) = r^2, where
+//   G(x) = sum_i max(x - v_i, 0)^2
+// is non-decreasing in x and non-increasing in every v_i: a value v_i >= x
+// adds nothing, which is the growth rule of Alg. 3.
+//
+// The result returned is the value x of the working precision at which
+// G_fl(x) comes nearest r^2 from either side (root_search), G_fl being G
+// evaluated with round-to-nearest operations in a fixed order (largest term
+// first; no contraction).  Every operation in G_fl is monotone in its
+// operands, so G_fl keeps both monotonicities, and the returned root is then
+// a monotone function of (a, b, c): a neighbour that is lower can never give
+// a higher root.  The discrete solution is the
+// greatest fixed point of psi_p = min(psi_p, root_p(neighbours)) below the
+// initial values (+inf off the sources); iterations of a monotone map from
+// above reach that one fixed point in any order, so psi does not depend on
+// the stride, the schedule, the block edge or the order of the marches, bit
+// for bit.
+//
+// The search starts from a fast estimate of the root, written without
+// cancellation: with k admitted values,
 //   x = v_1 + (sum_i (v_i - v_1) + sqrt(D)) / k,
 //   D = k r^2 - sum_{i<j} (v_i - v_j)^2          (Lagrange's identity),
 // whose differences are exact.  Whenever a value is admitted D > r^2 in
-// exact arithmetic, so D < tau*k*r^2 (tau < 1/3) only flags rounding trouble.
+// exact arithmetic, so D < tau*k*r^2 (tau < 1/3) only flags rounding trouble;
+// the estimate is then taken in double precision.  The estimate is within an
+// ulp or two of the result, so the search usually evaluates G_fl twice (at
+// the estimate and one ulp away): it gallops outwards from the estimate until
+// the result is bracketed, then bisects on the bit patterns (non-negative
+// values order like their bits).
 // ---------------------------------------------------------------------------
-// The root never falls below the largest admitted value (causality of the
-// upwind scheme; exact arithmetic guarantees it, rounding could break it by an
-// ulp and let two nodes lower each other forever), hence the fmax clamps.
-// (D clamped at 0 by its sign bit, and the division by 3 as a product: the
-// FP64 pipe of this part is narrow, so only the root's own arithmetic uses it)
 __device__ __forceinline__ double clamp0(double D) { return (ubits(D) >> 63) ? 0.0 : D; }
-__device__ __forceinline__ double upwind_root(double a, double b, double c, double r) {
+
+__device__ __forceinline__ float gsum(float x, float a, float b, float c) {
+    const float ta = fmaxf(__fsub_rn(x, a), 0.0f), tb = fmaxf(__fsub_rn(x, b), 0.0f);
+    const float tc = fmaxf(__fsub_rn(x, c), 0.0f);
+    return __fadd_rn(__fadd_rn(__fmul_rn(ta, ta), __fmul_rn(tb, tb)), __fmul_rn(tc, tc));
+}
+// (max with 0 by the sign bit: the FP64 pipe of this part is narrow)
+__device__ __forceinline__ double gsum(double x, double a, double b, double c) {
+    const double ta = clamp0(__dsub_rn(x, a)), tb = clamp0(__dsub_rn(x, b)), tc = clamp0(__dsub_rn(x, c));
+    return __dadd_rn(__dadd_rn(__dmul_rn(ta, ta), __dmul_rn(tb, tb)), __dmul_rn(tc, tc));
+}
+
+template <typename T>
+struct BitsOf;
+template <>
+struct BitsOf<float> {
+    using U = unsigned;
+    static constexpr U kInf = 0x7f800000u;
+};
+template <>
+struct BitsOf<double> {
+    using U = unsigned long long;
+    static constexpr U kInf = 0x7ff0000000000000ull;
+};
+
+// The root: with hi the smallest value of precision T above a with
+// gsum(hi) >= r2, and lo the value just below it (gsum(lo) < r2), the one of
+// the two whose gsum is nearer r2 (lo on a tie of the distances is not taken).
+// Near the root G is linear to far below an ulp of x, so this is the root
+// rounded to nearest, without the upward drift that always taking hi would
+// add at every step along a characteristic.  It stays monotone: lower values
+// (b, c, a) raise gsum everywhere, so hi cannot move up, and if it stays put
+// the distance r2 - gsum(lo) can only shrink and gsum(hi) - r2 only grow
+// (rounded subtraction is monotone), so lo can only become more likely.
+// Searched from the estimate x0.
+template <typename T>
+__device__ __forceinline__ T root_search(T x0, T a, T b, T c, T r2) {
+    using U = typename BitsOf<T>::U;
+    const U ua = ubits(a);
+    U g = ubits(x0);
+    if (!(g > ua) || g > BitsOf<T>::kInf) g = ua + 1;
+    U lo, hi;                       // gsum(lo) < r2 <= gsum(hi); lo = a needs no evaluation (G(a) = 0)
+    T glo, ghi;
+    U step = 1;
+    T gg = gsum(from_bits(g), a, b, c);
+    if (gg >= r2) {
+        hi = g;
+        ghi = gg;
+        for (;;) {
+            const U cand = (hi - ua > step) ? hi - step : ua;
+            if (cand == ua) {
+                lo = ua;
+                glo = 0;
+                break;
+            }
+            const T gc = gsum(from_bits(cand), a, b, c);
+            if (!(gc >= r2)) {
+                lo = cand;
+                glo = gc;
+                break;
+            }
+            hi = cand;
+            ghi = gc;
+            step <<= 1;
+        }
+    } else {
+        lo = g;
+        glo = gg;
+        for (;;) {
+            const U cand = (BitsOf<T>::kInf - lo > step) ? lo + step : BitsOf<T>::kInf;
+            const T gc = gsum(from_bits(cand), a, b, c);
+            if (cand == BitsOf<T>::kInf || gc >= r2) {
+                hi = cand;
+                ghi = gc;
+                break;
+            }
+            lo = cand;
+            glo = gc;
+            step <<= 1;
+        }
+    }
+    while (hi - lo > 1) {
+        const U mid = lo + ((hi - lo) >> 1);
+        const T gm = gsum(from_bits(mid), a, b, c);
+        if (gm >= r2) {
+            hi = mid;
+            ghi = gm;
+        } else {
+            lo = mid;
+            glo = gm;
+        }
+    }
+    return (r2 - glo < ghi - r2) ? from_bits(lo) : from_bits(hi);
+}
+
+// The estimate (with the causality clamps: in exact arithmetic the root is not
+// below the largest admitted value).  (The division by 3 as a product.)
+__device__ __forceinline__ double root_estimate(double a, double b, double c, double r) {
     double x = a + r;
     if (!vlt(b, x)) return x;
     const double d = b - a;
@@ -125,30 +241,44 @@ __device__ __forceinline__ double upwind_root(double a, double b, double c, doub
     return vmax(a + (d + e + sqrt(clamp0(D))) * (1.0 / 3.0), c);
 }
 
+__device__ __forceinline__ double upwind_root(double a, double b, double c, double r) {
+    return root_search<double>(root_estimate(a, b, c, r), a, b, c, __dmul_rn(r, r));
+}
+
 // FP32: sqrt(D) as D * rsqrt(D) (the hardware reciprocal square root, a few
 // ulp) and the division by 3 as a product; D >= tau*k*r^2 > 0 on this path
-// (the max guards tau = 0).
+// (the max guards tau = 0).  When (h/F)^2 underflows single precision the whole
+// root is taken in double precision and rounded (rounding is monotone too).
 __device__ __forceinline__ float sqrt_f32(float D) { return D * rsqrtf(fmaxf(D, FLT_MIN)); }
 
 __device__ __forceinline__ float upwind_root_f32(float a, float b, float c, float r, float tau, int& fb) {
+    const float r2 = __fmul_rn(r, r);
+    if (!(r2 >= FLT_MIN)) {
+        ++fb;
+        return static_cast<float>(upwind_root(a, b, c, r));
+    }
     float x = a + r;
-    if (!(x > b)) return x;
-    const float d = b - a;
-    const float r2 = r * r;
-    float D = 2.0f * r2 - d * d;
-    if (!(r2 >= FLT_MIN) || !(D >= tau * 2.0f * r2)) {
-        ++fb;
-        return static_cast<float>(upwind_root(a, b, c, r));
+    if (x > b) {
+        const float d = b - a;
+        float D = 2.0f * r2 - d * d;
+        if (!(D >= tau * 2.0f * r2)) {
+            ++fb;
+            x = static_cast<float>(root_estimate(a, b, c, r));
+        } else {
+            x = fmaxf(a + (d + sqrt_f32(D)) * 0.5f, b);
+            if (x > c) {
+                const float e = c - a, g = c - b;
+                D = 3.0f * r2 - (d * d + e * e + g * g);
+                if (!(D >= tau * 3.0f * r2)) {
+                    ++fb;
+                    x = static_cast<float>(root_estimate(a, b, c, r));
+                } else {
+                    x = fmaxf(a + (d + e + sqrt_f32(D)) * (1.0f / 3.0f), c);
+                }
+            }
+        }
     }
-    x = fmaxf(a + (d + sqrt_f32(D)) * 0.5f, b);
-    if (!(x > c)) return x;
-    const float e = c - a, g = c - b;
-    D = 3.0f * r2 - (d * d + e * e + g * g);
-    if (!(D >= tau * 3.0f * r2)) {
-        ++fb;
-        return static_cast<float>(upwind_root(a, b, c, r));
-    }
-    return fmaxf(a + (d + e + sqrt_f32(D)) * (1.0f / 3.0f), c);
+    return root_search<float>(x, a, b, c, r2);
 }
 
 // Bounds arrive as doubles; a float node value v satisfies v <= b exactly when
@@ -996,6 +1126,34 @@ __device__ __forceinline__ int barrier_poll(Ctrl* C, int lane, unsigned gen) {
     return __shfl_sync(0xffffffffu, state, 0);
 }
 
+// A warp that gives up on a wait: the status bit, made visible to every other
+// warp of the launch before the warp leaves.
+__device__ __forceinline__ void give_up(Ctrl* C, int lane) {
+    if (lane == 0) {
+        atomicOr(&C->status, kStWaitTimeout);
+        __threadfence();
+    }
+    __syncwarp();
+}
+
+// Start of CTA-wide work (16^3 blocks) in a restart: whether the whole CTA may
+// go on.  A warp that gives up on a wait (give_up) exits on its own, and an
+// exiting thread releases a CTA barrier that waits only for it (the exit rule
+// of PTX), so this vote completes whichever warps are still there.  Every
+// thread of the CTA gets the same answer: false if a warp is missing, if a
+// warp of the CTA brings ok = false, or if any wait of the launch has run out.
+// The CTA then leaves as a whole, before its first CTA-wide march, and no
+// thread is ever left waiting at a CTA barrier for a warp that has gone.
+// s_arrived is a shared counter that starts at zero (and is zero again after).
+__device__ __forceinline__ bool cta_go(const Ctrl* C, bool ok, int lane, int* s_arrived) {
+    if (lane == 0) atomicAdd(s_arrived, 1);
+    const int stop = __syncthreads_or((!ok || (__ldcg(&C->status) & kStWaitTimeout)) ? 1 : 0);
+    const bool all = *reinterpret_cast<volatile int*>(s_arrived) == static_cast<int>(blockDim.x >> 5);
+    __syncthreads();
+    if (threadIdx.x == 0) *s_arrived = 0;
+    return stop == 0 && all;
+}
+
 // A grid barrier inside a restart (no bookkeeping): every warp of the launch
 // arrives; false if this or another wait ran out (the status then says so).
 __device__ inline bool grid_sync(Ctrl* C, int lane, long long limit) {
@@ -1010,7 +1168,7 @@ __device__ inline bool grid_sync(Ctrl* C, int lane, long long limit) {
         if (st == 1) return true;
         if (st == 2) return false;
         if (it > limit) {
-            if (lane == 0) atomicOr(&C->status, kStWaitTimeout);
+            give_up(C, lane);
             return false;
         }
         __nanosleep(nap);

@@ -1,22 +1,26 @@
 // eik_solve_noalloc: one solve that allocates no device memory.
 //
-// Some callers cannot call cudaMalloc: code running under a caching allocator
-// or a memory pool they do not own, code inside a CUDA stream capture, and
-// embedders that must not grow the process's device footprint at solve time.
-// For them this entry point keeps every piece of working memory of a solve
-// (h/F in brick layout, the two psi copies of each brick, the Upsilon masks,
-// stamps, work lists, control block and the fixed-node tables) in one
-// file-scope device array of fixed size.  The caller passes the speeds and the
-// output buffer, both in device memory.
+// Some callers cannot call cudaMalloc while they solve: code that runs under a
+// caching allocator or a memory pool it does not own (an allocation there
+// takes memory behind the pool's back, or fails once the pool has reserved
+// the device), and embedders that must not grow the process's device
+// footprint at solve time.  For them this entry point keeps every piece of
+// working memory of a solve (h/F in brick layout, the two psi copies of each
+// brick, the Upsilon masks, stamps, work lists, control block and the
+// fixed-node tables) in one file-scope device array of fixed size, and its
+// host-side set-up uses fixed-size arrays on the stack.  The caller passes the
+// speeds and the output buffer, both in device memory.
 //
 // The array is part of the library image: every GPU that loads libeik holds
-// it until the process exits.  Its device address is looked up once per
-// device, on the first call made with that device current; make that first
-// call before any stream capture.  All calls share the array and it keeps the
-// last call's contents, so calls that overlap on the GPU (two host threads,
-// or asynchronous work on two streams) race; each call clears what must start
-// from zero (stamps, work-list state, control block) itself.
+// it until the process exits.  Host code cannot use the array's name as a
+// device address, so its address is looked up with cudaGetSymbolAddress once
+// per device, on the first call made with that device current; make that
+// first call before any stream capture.  All calls share the array and it
+// keeps the last call's contents, so calls that overlap on the GPU (two host
+// threads, or asynchronous work on two streams) race; each call clears what
+// must start from zero (stamps, work-list state, control block) itself.
 #include "eik.h"
+#include "eik_host.h"
 #include "eik_internal.cuh"
 
 #include <algorithm>
@@ -119,19 +123,6 @@ Layout layout_for(int64_t nb) {
     return L;
 }
 
-int cell_nodes(double s, double h, int n, int out[2]) {
-    const double t = s / h;
-    const double tn = std::floor(t + 0.5);
-    if (std::fabs(t - tn) <= 1e-9) {
-        out[0] = std::min(std::max(static_cast<int>(tn), 0), n - 1);
-        return 1;
-    }
-    const int i0 = std::min(std::max(static_cast<int>(std::floor(t)), 0), std::max(n - 2, 0));
-    out[0] = i0;
-    out[1] = std::min(i0 + 1, n - 1);
-    return (out[1] == out[0]) ? 1 : 2;
-}
-
 }  // namespace
 
 extern "C" {
@@ -148,14 +139,18 @@ eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float* F, in
     eik_params P;
     eik_params_default(&P);
     if (params) P = *params;
-    if (!(P.stride > 0.0)) return fail(EIK_EINVAL, "eik_solve_noalloc: stride must be > 0");
+    if (!(P.stride > 0.0)) return fail(EIK_EINVAL, "eik_solve_noalloc: stride must be > 0 (+inf allowed)");
+    {
+        eik_status code;
+        if (const char* m = eikh::param_error(P, &code)) return fail(code, std::string("eik_solve_noalloc: ") + m);
+    }
     if (P.block_dim != 0 && P.block_dim != 8) return fail(EIK_ENOTSUP, "eik_solve_noalloc: block_dim must be 8");
     if (P.schedule != EIK_SCHED_FIXED) return fail(EIK_ENOTSUP, "eik_solve_noalloc: fixed-stride schedule only");
+    if (P.log_restarts)
+        return fail(EIK_ENOTSUP, "eik_solve_noalloc: no restart log (its records would need memory)");
     if (P.window == 0.0) P.window = 2.0;
-    if (!(P.window > 0.0) || !std::isfinite(P.window)) return fail(EIK_EINVAL, "eik_solve_noalloc: bad window");
     if (P.width == 0.0) P.width = INFINITY;
-    if (!(P.width > 0.0)) return fail(EIK_EINVAL, "eik_solve_noalloc: width must be >= 0 (0 = +inf)");
-    if (P.max_restarts <= 0) P.max_restarts = int64_t(1) << 24;
+    if (P.max_restarts == 0) P.max_restarts = int64_t(1) << 24;
     const int nx = dims[0], ny = dims[1], nz = dims[2];
     const int BX = (nx + 7) / 8, BY = (ny + 7) / 8, BZ = (nz + 7) / 8;
     const int64_t nb = int64_t(BX) * BY * BZ;
@@ -197,24 +192,14 @@ eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float* F, in
     NA_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
     NA_CK(eikg::launch_layout_speed<float>(F, rr, nx, ny, nz, BX, BY, nb, h, err, 1, st));
     NA_CK(cudaMemcpyAsync(&bad, err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    // fixed nodes: the nodes of each source's cell, psi0 = distance / F
-    double cd[kMaxFix];
+    // fixed nodes (Alg. 1): the nodes of each source's cell with their h/F, psi0 = distance / F
+    const eikh::Bricks geo{BX, BY, BZ, 0};
+    eikh::Cand cand[kMaxFix];
+    const int nc = eikh::source_candidates_into(xyz, nsrc, nx, ny, nz, h, geo, cand);
     int32_t cb[kMaxFix], cp[kMaxFix];
-    int nc = 0;
-    for (int q = 0; q < nsrc; ++q) {
-        const double* xs = xyz + 3 * q;
-        int cx[2], cy[2], cz[2];
-        const int mx = cell_nodes(xs[0], h, nx, cx), my = cell_nodes(xs[1], h, ny, cy), mz = cell_nodes(xs[2], h, nz, cz);
-        for (int a = 0; a < mz; ++a)
-            for (int b2 = 0; b2 < my; ++b2)
-                for (int d = 0; d < mx; ++d) {
-                    const int i = cx[d], j = cy[b2], k = cz[a];
-                    const double dx = i * h - xs[0], dy = j * h - xs[1], dz = k * h - xs[2];
-                    cd[nc] = std::sqrt(dx * dx + dy * dy + dz * dz);
-                    cb[nc] = ((k >> 3) * BY + (j >> 3)) * BX + (i >> 3);
-                    cp[nc] = ((k & 7) * 8 + (j & 7)) * 8 + (i & 7);
-                    ++nc;
-                }
+    for (int t = 0; t < nc; ++t) {
+        cb[t] = cand[t].b;
+        cp[t] = cand[t].p;
     }
     double cr[kMaxFix];
     NA_CK(cudaMemcpyAsync(d_fb, cb, nc * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -223,47 +208,18 @@ eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float* F, in
     NA_CK(cudaMemcpyAsync(cr, d_cr, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
     NA_CK(cudaStreamSynchronize(st));
     if (bad) return fail(EIK_EINVAL, "eik_solve_noalloc: F must be finite and >= 0 everywhere");
-    // keep the smallest psi0 per node
-    int32_t fb[kMaxFix], fp[kMaxFix];
-    double fv[kMaxFix];
-    int nfix = 0;
-    for (int t = 0; t < nc; ++t) {
-        double v;
-        if (cd[t] == 0.0) v = 0.0;
-        else if (std::isfinite(cr[t]) && cr[t] > 0.0) v = cd[t] * cr[t] / h;
-        else continue;
-        int at = -1;
-        for (int u = 0; u < nfix; ++u)
-            if (fb[u] == cb[t] && fp[u] == cp[t]) at = u;
-        if (at < 0) {
-            fb[nfix] = cb[t];
-            fp[nfix] = cp[t];
-            fv[nfix] = v;
-            ++nfix;
-        } else if (v < fv[at]) {
-            fv[at] = v;
-        }
-    }
+    eikh::FixNode fix[kMaxFix];
+    const int nfix = eikh::fixed_nodes_into(cand, nc, cr, h, fix);
     // bricks with fixed nodes, and the work list of restart 1
     int32_t sb[kMaxFix], enq[7 * kMaxFix];
     int nsb = 0, nenq = 0;
-    auto add_unique = [](int32_t* a, int& n, int32_t v) {
-        for (int i = 0; i < n; ++i)
-            if (a[i] == v) return;
-        a[n++] = v;
-    };
+    eikh::first_active_into(fix, nfix, geo, sb, &nsb, enq, &nenq);
+    int32_t fb[kMaxFix], fp[kMaxFix];
+    double fv[kMaxFix];
     for (int t = 0; t < nfix; ++t) {
-        const int32_t b = fb[t];
-        add_unique(sb, nsb, b);
-        add_unique(enq, nenq, b);
-        const int x = fp[t] & 7, y = (fp[t] >> 3) & 7, z = fp[t] >> 6;
-        const int bx = b % BX, by = (b / BX) % BY, bz = b / (BX * BY);
-        if (x == 0 && bx > 0) add_unique(enq, nenq, b - 1);
-        if (x == 7 && bx < BX - 1) add_unique(enq, nenq, b + 1);
-        if (y == 0 && by > 0) add_unique(enq, nenq, b - BX);
-        if (y == 7 && by < BY - 1) add_unique(enq, nenq, b + BX);
-        if (z == 0 && bz > 0) add_unique(enq, nenq, b - BX * BY);
-        if (z == 7 && bz < BZ - 1) add_unique(enq, nenq, b + BX * BY);
+        fb[t] = fix[t].b;
+        fp[t] = fix[t].p;
+        fv[t] = fix[t].v;
     }
     eikg::Ctrl H;
     std::memset(&H, 0, sizeof(H));
@@ -323,13 +279,15 @@ eik_status eik_solve_noalloc(const int32_t dims[3], double h, const float* F, in
         L.width = P.width;
         L.fallback_tau = P.fallback_tau;
         L.max_restarts = P.max_restarts;
-        L.wait_limit = eikg::kWaitPolls;
+        L.wait_limit = P.wait_polls > 0 ? P.wait_polls : eikg::kWaitPolls;
         L.sched = EIK_SCHED_FIXED;
         L.mlp = nullptr;
         L.h = h;
         L.nmax = std::max(nx, std::max(ny, nz));
         L.seed = 0;
+        if (P.loop_events[0]) NA_CK(cudaEventRecord(static_cast<cudaEvent_t>(P.loop_events[0]), st));
         NA_CK(eikg::launch_restart_loop<float>(L, per_sm * sms, st));
+        if (P.loop_events[1]) NA_CK(cudaEventRecord(static_cast<cudaEvent_t>(P.loop_events[1]), st));
     }
     if (nfix > 0) NA_CK(eikg::launch_restore_r<float>(nfix, d_fb, d_fp, d_saved, rr, st));
     NA_CK(eikg::launch_result<float>(slot, stampv, psi_out, nx, ny, 0, nz, BX, BY, st));

@@ -10,6 +10,8 @@
 #include "eik_internal.cuh"
 #include "eik_mlp.cuh"
 
+#include "eik_sched_weights.inc"   // kSchedDefault: the shipped schedule-network weights (written by build.py)
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -89,6 +91,8 @@ struct eik_ctx {
     bool in_flight = false;
     bool speed_unchecked = false;  // an eik_set_speed_async whose validation flag is not read yet
     int64_t last_nr = 0;
+    int tuned_block = 0;           // block edge picked by eik_autotune (0: not tuned)
+    double tuned_stride = 0.0;     // stride picked by eik_autotune
     int loop_grid = 0;
     int sms = 0;
     eik_params params{};
@@ -297,6 +301,12 @@ eik_status eik_create(eik_ctx** out, const int32_t dims[3], double h, const void
     if (e != cudaSuccess || per_sm < 1)
         return bail(EIK_ECUDA, std::string("eik_create: occupancy query: ") + cudaGetErrorString(e));
     c->loop_grid = per_sm * c->sms;
+    // every context starts with the shipped schedule network (eik_set_schedule replaces or unloads it)
+    static_assert(EIK_SCHED_DEFAULT_COUNT == eikg::kParams, "shipped weights match the network");
+    e = cudaMalloc(&c->d_mlp, sizeof(float) * eikg::kParams);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_mlp, kSchedDefault, sizeof(float) * eikg::kParams, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(EIK_ENOMEM, std::string("eik_create: schedule weights: ") + cudaGetErrorString(e));
     *out = c;
     return EIK_OK;
 }
@@ -596,19 +606,10 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
 
 eik_status check_params(eik_ctx* c, const eik_params* p) {
     if (!p) return fail(c, EIK_EINVAL, "params is NULL");
-    if (!(p->stride > 0.0)) return fail(c, EIK_EINVAL, "stride must be > 0 (+inf allowed)");
-    if (p->block_dim != 0 && p->block_dim != 8 && p->block_dim != 16)
-        return fail(c, EIK_ENOTSUP, "block_dim must be 8 or 16 (or 0)");
-    if (p->schedule != EIK_SCHED_FIXED && p->schedule != EIK_SCHED_LEARNED && p->schedule != EIK_SCHED_RANDOM)
-        return fail(c, EIK_EINVAL, "schedule must be EIK_SCHED_FIXED, EIK_SCHED_LEARNED or EIK_SCHED_RANDOM");
+    eik_status code;
+    if (const char* m = eikh::param_error(*p, &code)) return fail(c, code, m);
     if (p->schedule == EIK_SCHED_LEARNED && !c->d_mlp)
-        return fail(c, EIK_ESTATE, "learned schedule requested but no weights were loaded (eik_set_schedule)");
-    if (!(p->window >= 0.0) || !std::isfinite(p->window)) return fail(c, EIK_EINVAL, "window must be finite and >= 0");
-    if (!(p->fallback_tau >= 0.0) || !(p->fallback_tau <= 1.0))
-        return fail(c, EIK_EINVAL, "fallback_tau must lie in [0, 1]");
-    if (p->max_restarts < 0) return fail(c, EIK_EINVAL, "max_restarts must be >= 0");
-    if (!(p->width >= 0.0)) return fail(c, EIK_EINVAL, "width must be >= 0 (0 = +inf)");
-    if (p->wait_polls < 0) return fail(c, EIK_EINVAL, "wait_polls must be >= 0 (0 = default)");
+        return fail(c, EIK_ESTATE, "learned schedule requested but the weights were unloaded (eik_set_schedule)");
     return EIK_OK;
 }
 
@@ -619,13 +620,21 @@ extern "C" {
 eik_status eik_solve_async(eik_ctx* c, const eik_params* params) {
     if (!c) return fail(nullptr, EIK_EINVAL, "eik_solve_async: ctx is NULL");
     if (c->in_flight) return fail(c, EIK_ESTATE, "eik_solve_async: a solve is already in flight");
-    eik_status st = check_params(c, params);
+    if (!params) return fail(c, EIK_EINVAL, "params is NULL");
+    eik_params P = *params;
+    // stride 0: the learned schedule (its first two restarts advance the bound by 2h)
+    if (P.stride == 0.0) {
+        P.schedule = EIK_SCHED_LEARNED;
+        P.stride = 2.0 * c->h;
+    }
+    eik_status st = check_params(c, &P);
     if (st != EIK_OK) return st;
     if (c->src.empty()) return fail(c, EIK_ESTATE, "eik_solve: no source added");
     st = check_speed(c);
     if (st != EIK_OK) return st;
-    eik_params P = *params;
-    if (P.block_dim == 0) P.block_dim = 8;
+    // block edge 0: under the learned schedule the network picks it from restart 3 on (8 before); under a
+    // fixed stride the edge eik_autotune picked for this context, else 8
+    if (P.block_dim == 0) P.block_dim = (P.schedule == EIK_SCHED_FIXED && c->tuned_block) ? c->tuned_block : 8;
     if (P.max_restarts == 0) P.max_restarts = int64_t(1) << 24;
     if (P.window == 0.0) P.window = 2.0;
     if (P.width == 0.0) P.width = INFINITY;
@@ -687,6 +696,58 @@ eik_status eik_solve(eik_ctx* c, double stride, int32_t block_dim, eik_stats* st
     p.stride = stride;
     p.block_dim = block_dim;
     return eik_solve_ex(c, &p, stats);
+}
+
+eik_status eik_autotune(eik_ctx* c, int32_t rounds, double* stride_out, int32_t* block_out, double* best_ms) {
+    if (!c) return fail(nullptr, EIK_EINVAL, "eik_autotune: ctx is NULL");
+    if (c->in_flight) return fail(c, EIK_ESTATE, "eik_autotune: a solve is in flight");
+    if (rounds < 0) return fail(c, EIK_EINVAL, "eik_autotune: rounds must be >= 0");
+    if (c->src.empty()) return fail(c, EIK_ESTATE, "eik_autotune: no source added");
+    struct Cand {
+        double stride_h;
+        int block;
+        std::vector<double> ms;
+    };
+    std::vector<Cand> alive;
+    for (double sh : {1.0, 1.5, 2.0, 2.5, 3.0, 4.0})
+        for (int bd : {8, 16}) alive.push_back({sh, bd, {}});
+    const eik_params keep = c->params;
+    auto median = [](std::vector<double> v) {
+        std::sort(v.begin(), v.end());
+        return v[v.size() / 2];
+    };
+    int reps = 1;
+    for (int round = 0; alive.size() > 1 && (rounds == 0 || round < rounds); ++round, reps *= 2) {
+        for (auto& cd : alive) {
+            for (int r = 0; r < reps; ++r) {
+                eik_params P;
+                eik_params_default(&P);
+                P.stride = cd.stride_h * c->h;
+                P.block_dim = cd.block;
+                eik_stats st{};
+                const eik_status e = eik_solve_ex(c, &P, &st);
+                if (e == EIK_ETIMEOUT) {
+                    cd.ms.push_back(INFINITY);
+                    continue;
+                }
+                if (e != EIK_OK) {
+                    c->params = keep;
+                    return e;
+                }
+                cd.ms.push_back(st.device_ms);
+            }
+        }
+        std::sort(alive.begin(), alive.end(), [&](const Cand& a, const Cand& b) { return median(a.ms) < median(b.ms); });
+        const size_t next = std::max<size_t>(1, alive.size() / 3);
+        alive.resize(next);
+    }
+    if (!std::isfinite(median(alive[0].ms))) return fail(c, EIK_ETIMEOUT, "eik_autotune: every candidate hit a cap");
+    c->tuned_stride = alive[0].stride_h * c->h;
+    c->tuned_block = alive[0].block;
+    if (stride_out) *stride_out = c->tuned_stride;
+    if (block_out) *block_out = c->tuned_block;
+    if (best_ms) *best_ms = median(alive[0].ms);
+    return EIK_OK;
 }
 
 eik_status eik_restart_log(eik_ctx* c, eik_restart_rec* out, int64_t cap, int64_t* n) {

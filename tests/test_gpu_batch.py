@@ -114,10 +114,7 @@ def test_batch_equals_single_grid_path(eik):
                 S.solve(tiles[i][1], block_dim=tiles[i][0])
                 one = S.result()
             got = B.result(i)
-            fin = np.isfinite(one)
-            assert np.array_equal(np.isfinite(got), fin)
-            if fin.any():
-                assert np.max(np.abs(got[fin] - one[fin]) / np.maximum(one[fin], 1e-300)) <= TOL64
+            assert np.array_equal(got, one)
     torch.cuda.synchronize()
 
 
@@ -215,6 +212,4 @@ def test_full_size_batch_64(eik, orc):
                 eik.eik_result(S.ctx, one)
             torch.cuda.synchronize()
             a, b = out.cpu().numpy(), one.cpu().numpy()
-            fin = np.isfinite(b)
-            assert np.array_equal(np.isfinite(a), fin), w.name
-            assert float(np.max(np.abs(a[fin] - b[fin]))) <= 2 * TOL32 * float(b[fin].max()), w.name
+            assert np.array_equal(a, b), w.name

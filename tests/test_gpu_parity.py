@@ -194,16 +194,62 @@ def test_group_blocks_cut_refreshes(eik, orc):
     assert s16["accepted"] < s8["accepted"] and s16["solves"] < s8["solves"]
 
 
-def test_stride_does_not_change_the_solution(eik):
-    """Sec. 2.4: the stride only schedules work; every stride reaches the same discrete solution."""
-    w = synth.workload("C3", 64)
+@pytest.mark.parametrize("cfg,n", [("C3", 64), ("C4", 96), ("C2", 128), ("C4", 192)])
+def test_schedule_does_not_change_the_solution(eik, cfg, n):
+    """Sec. 2.4: the stride only schedules work.  The root of Alg. 3 is evaluated as a monotone function of
+    the neighbour values, so every stride, block edge, schedule and acceptance window reaches the same
+    discrete solution bit for bit."""
+    w = synth.workload(cfg, n)
     F = w.speed()
     base, _ = run(eik, F, w.h, w.sources, "fp32", 2 * w.h)
-    for s, bd in ((0.5, 8), (1.0, 8), (4.0, 8), (16.0, 8), (math.inf, 8), (2.0, 16), (8.0, 16)):
-        psi, _ = run(eik, F, w.h, w.sources, "fp32", s * w.h, block_dim=bd)
-        fin = np.isfinite(base)
-        assert np.array_equal(np.isfinite(psi), fin)
-        assert np.max(np.abs(psi[fin] - base[fin])) <= 4 * np.spacing(np.float32(base[fin].max()))
+    variants = [dict(stride=s * w.h, block_dim=bd) for s, bd in
+                ((0.5, 8), (1.0, 8), (1.5, 8), (4.0, 8), (16.0, 8), (math.inf, 8), (1.0, 16), (2.0, 16), (8.0, 16))]
+    variants += [dict(stride=2 * w.h, window=1 / math.sqrt(3)), dict(stride=2 * w.h, window=4.0),
+                 dict(stride=0.0, block_dim=0),                                  # the learned schedule
+                 dict(stride=2 * w.h, schedule=eik.EIK_SCHED_RANDOM, seed=11)]   # 8^3 and 16^3 restarts mixed
+    for v in variants:
+        kw = dict(v)
+        stride = kw.pop("stride")
+        psi, _ = run(eik, F, w.h, w.sources, "fp32", stride, **kw)
+        assert np.array_equal(psi, base), (v, int(np.sum(psi != base)))
+
+
+def test_fp64_schedule_does_not_change_the_solution(eik):
+    w = synth.workload("C4", 72)
+    F = synth.round_to(w.speed(), "fp64")
+    base, _ = run(eik, F, w.h, w.sources, "fp64", 2 * w.h)
+    for s, bd in ((0.5, 8), (4.0, 8), (math.inf, 8), (2.0, 16)):
+        psi, _ = run(eik, F, w.h, w.sources, "fp64", s * w.h, block_dim=bd)
+        assert np.array_equal(psi, base), (s, bd)
+
+
+def test_stride_zero_is_the_learned_schedule(eik, orc):
+    """eik_solve(ctx, 0, 0): the learned schedule with the weights a new context holds, picking stride and
+    block edge per restart; same solution as the oracle within the FP32 bar, and as a fixed stride bit for bit."""
+    import torch
+    w = synth.workload("C3", 96)
+    F = w.speed()
+    ref = orc.fmm(F, w.h, w.sources)
+    Fd = torch.from_numpy(F.astype(np.float32)).cuda()
+    ctx = eik.eik_create(w.dims, w.h, Fd, "fp32")
+    try:
+        eik.eik_add_sources(ctx, w.sources)
+        st = eik.eik_solve(ctx, 0.0, 0)
+        out = torch.empty_like(Fd)
+        eik.eik_result(ctx, out)
+        learned = out.double().cpu().numpy()
+        st_f = eik.eik_solve(ctx, 2 * w.h, 8)
+        eik.eik_result(ctx, out)
+        fixed = out.double().cpu().numpy()
+        eik.eik_set_schedule(ctx, None)                     # unloaded weights: stride 0 is refused
+        with pytest.raises(eik.EikError) as e:
+            eik.eik_solve(ctx, 0.0, 0)
+        assert e.value.status == eik.EIK_ESTATE
+    finally:
+        eik.eik_destroy(ctx)
+    assert st["status"] == 0 and st["restarts"] != st_f["restarts"]
+    assert_parity(learned, ref, "fp32")
+    assert np.array_equal(learned, fixed)
 
 
 def test_window_zero_is_the_papers_order(eik, orc):
@@ -243,13 +289,16 @@ def test_error_paths(eik):
             eik.eik_add_sources(ctx, [[0.5, 0.5, 1.5]])
         assert e.value.status == eik.EIK_EINVAL
         eik.eik_add_sources(ctx, [[0.5, 0.5, 0.5]])
-        for bad in (0.0, -1.0, float("nan")):
+        for bad in (-1.0, float("nan"), -float("inf")):
             with pytest.raises(eik.EikError) as e:
                 eik.eik_solve(ctx, bad)
             assert e.value.status == eik.EIK_EINVAL
         with pytest.raises(eik.EikError) as e:
             eik.eik_solve_ex(ctx, 0.25, max_restarts=2)
         assert e.value.status == eik.EIK_ETIMEOUT
+        with pytest.raises(eik.EikError) as e:
+            eik.eik_solve(ctx, 0.25, 12)
+        assert e.value.status == eik.EIK_ENOTSUP
         st = eik.eik_solve(ctx, 0.25)
         assert st["status"] == 0
     finally:
@@ -347,11 +396,14 @@ def test_full_size_local_equation_on_samples(eik, orc, cfg, n):
     assert gap <= 8 * 2.0 ** -24, gap
 
 
-def test_device_waits_give_up_and_the_context_stays_usable(eik, orc):
+@pytest.mark.parametrize("kw", [dict(block_dim=8), dict(block_dim=16),
+                                dict(block_dim=8, schedule=1), dict(block_dim=8, schedule=2, seed=3)],
+                         ids=["blocks8", "blocks16", "learned", "random"])
+def test_device_waits_give_up_and_the_context_stays_usable(eik, orc, kw):
     """Failure detection without a GPU fault: with a limit of one poll, the device-side waits (the grid
-    barrier, a neighbour's march, a work-list entry) run out; the kernel records it, every warp returns,
-    the solve reports EIK_ETIMEOUT, and the next solve on the same context is correct.  (8^3 blocks only:
-    that path has no CTA-wide barrier that a returning warp could leave waiting.)"""
+    barrier, a neighbour's march, a work-list entry, the group-list barrier) run out; the kernel records it,
+    every warp returns -- on the 16^3 path a CTA leaves as a whole, after a vote at the start of the restart --
+    the solve reports EIK_ETIMEOUT, and the next solve on the same context is correct."""
     w = synth.workload("C2", 96)
     F = w.speed()
     Fh = np.ascontiguousarray(F.astype(np.float32))
@@ -359,12 +411,12 @@ def test_device_waits_give_up_and_the_context_stays_usable(eik, orc):
     try:
         eik.eik_add_sources(ctx, w.sources)
         with pytest.raises(eik.EikError) as e:
-            eik.eik_solve_ex(ctx, w.h, block_dim=8, wait_polls=1)
+            eik.eik_solve_ex(ctx, w.h, wait_polls=1, **kw)
         assert e.value.status == eik.EIK_ETIMEOUT
         assert "wait limit" in str(e.value)
         with pytest.raises(eik.EikError, match="no successful solve"):
             eik.eik_result(ctx, np.empty_like(Fh))
-        eik.eik_solve_ex(ctx, 2 * w.h, block_dim=8)
+        eik.eik_solve_ex(ctx, 2 * w.h, **kw)
         psi = np.empty_like(Fh)
         eik.eik_result(ctx, psi)
     finally:

@@ -60,9 +60,7 @@ def test_learned_schedule_versus_fixed_stride(eik):
         finally:
             eik.eik_destroy(ctx)
         a, b = a.cpu().numpy(), b.cpu().numpy()
-        fin = np.isfinite(a)
-        assert np.array_equal(fin, np.isfinite(b))
-        assert np.max(np.abs(a[fin] - b[fin])) <= 4 * np.spacing(np.float32(a[fin].max()))
+        assert np.array_equal(a, b)                             # the schedule does not change psi
         assert sl["restarts"] != sf["restarts"]                 # the schedule adapts the stride
         tot_fixed += sf["device_ms"]
         tot_learned += sl["device_ms"]

@@ -1,14 +1,18 @@
-"""The allocation-free solve entry point agrees with the regular one.
+"""The allocation-free solve entry point agrees with the regular one and with the oracle.
 
 eik_solve_noalloc exists for callers that cannot allocate device memory while
-they solve (memory pools or caching allocators they do not own, stream
-capture, fixed device footprints).  It keeps its working memory in a fixed
-array inside the library.  This test calls it through the C ABI twice in a row
-(the second call reuses the array the first one left behind) and compares each
-result with eik_create / eik_solve / eik_result on the same input, within the
-FP32 tolerance of the parity tests (1e-5 * max psi).  It also checks that a
-grid above the array's limit is refused with EIK_EINVAL.  The file is named so
-that pytest collects it last.
+they solve: code under a memory pool or caching allocator it does not own, and
+embedders that keep the process's device footprint fixed.  It keeps its working
+memory in a fixed array inside the library.  This test calls it through the C
+ABI twice in a row (the second call reuses the array the first one left
+behind) and compares each result with eik_create / eik_solve / eik_result on
+the same input -- bit for bit, since both run the same kernels on the same
+discrete problem -- and with the FP64 oracle within the FP32 bar of the parity
+tests (1e-5 * max psi).  It checks that the device's free memory does not move
+across a call, that a grid above the array's limit and bad parameters are
+refused, and that a call whose device waits run out (wait_polls = 1) reports
+EIK_ETIMEOUT and leaves the next call correct.  The file is named so that
+pytest collects it last.
 """
 import ctypes as C
 
@@ -51,44 +55,86 @@ def regular(eik, w, Fd, stride):
         eik.eik_destroy(ctx)
 
 
-def noalloc(eik, w, Fd, stride):
+def call(eik, w, Fd, out, stride, **kw):
+    """eik_solve_noalloc through the C ABI into the caller's device buffer `out`; returns (status, stats)."""
     import torch
     L = eik.lib()
-    out = torch.full_like(Fd, -1.0)
     d = (C.c_int32 * 3)(*w.dims)
     src = np.ascontiguousarray(np.asarray(w.sources, dtype=np.float64).reshape(-1, 3))
     p = eik.eik_params_default()
     p.stride = stride
+    for k, v in kw.items():
+        setattr(p, k, v)
     st = eik.eik_stats()
     rc = L.eik_solve_noalloc(d, w.h, C.c_void_p(Fd.data_ptr()), len(src),
                              src.ctypes.data_as(C.POINTER(C.c_double)), C.byref(p), C.c_void_p(out.data_ptr()),
                              C.byref(st), C.c_void_p(torch.cuda.current_stream().cuda_stream))
-    assert rc == eik.EIK_OK, L.eik_noalloc_last_error().decode()
     torch.cuda.synchronize()
-    return out.cpu().numpy(), st
+    return rc, st
 
 
-def close(a, b):
-    fin = np.isfinite(b)
-    assert np.array_equal(np.isfinite(a), fin)
-    return float(np.max(np.abs(a[fin] - b[fin]))) <= 1e-5 * float(b[fin].max())
-
-
-def test_noalloc_matches_regular_solve_twice(eik):
+def test_noalloc_matches_regular_solve_and_oracle_twice(eik, orc):
     import torch
-    cases = [synth.workload("C4", 72), synth.workload("C2", 61)]
-    for w in cases:
-        Fd = torch.from_numpy(w.speed().astype(np.float32)).cuda()
+    for w in (synth.workload("C4", 72), synth.workload("C2", 61)):
+        F = w.speed()
+        Fd = torch.from_numpy(F.astype(np.float32)).cuda()
         ref = regular(eik, w, Fd, 2 * w.h)
+        oref = orc.fmm(F, w.h, w.sources)
+        fin = np.isfinite(oref)
         for _ in range(2):                      # the second call starts from the first call's leftovers
-            got, st = noalloc(eik, w, Fd, 2 * w.h)
+            out = torch.full_like(Fd, -1.0)
+            rc, st = call(eik, w, Fd, out, 2 * w.h)
+            assert rc == eik.EIK_OK, eik.lib().eik_noalloc_last_error().decode()
             assert st.status == 0 and st.restarts > 0
-            assert close(got, ref)
+            got = out.cpu().numpy()
+            assert np.array_equal(got, ref)
+            assert np.array_equal(np.isfinite(got), fin)
+            assert float(np.max(np.abs(got[fin] - oref[fin]))) <= 1e-5 * float(oref[fin].max())
 
 
-def test_noalloc_rejects_grids_above_its_limit(eik):
+def test_noalloc_leaves_device_memory_untouched(eik):
+    """After a first call (which loads the kernels and looks up the array's address), a call changes the
+    device's free memory by nothing."""
+    import torch
+    w = synth.workload("C3", 80)
+    Fd = torch.from_numpy(w.speed().astype(np.float32)).cuda()
+    out = torch.empty_like(Fd)
+    rc, _ = call(eik, w, Fd, out, 2 * w.h)
+    assert rc == eik.EIK_OK
+    torch.cuda.synchronize()
+    before = torch.cuda.mem_get_info()[0]
+    rc, _ = call(eik, w, Fd, out, 2 * w.h)
+    assert rc == eik.EIK_OK
+    after = torch.cuda.mem_get_info()[0]
+    assert after == before, (before, after)
+
+
+def test_noalloc_timeout_then_a_correct_call(eik):
+    import torch
+    w = synth.workload("C2", 96)
+    Fd = torch.from_numpy(w.speed().astype(np.float32)).cuda()
+    ref = regular(eik, w, Fd, 2 * w.h)
+    out = torch.empty_like(Fd)
+    rc, st = call(eik, w, Fd, out, w.h, wait_polls=1)
+    assert rc == eik.EIK_ETIMEOUT and st.status == eik.EIK_ETIMEOUT
+    rc, _ = call(eik, w, Fd, out, 2 * w.h)
+    assert rc == eik.EIK_OK
+    assert np.array_equal(out.cpu().numpy(), ref)
+
+
+def test_noalloc_rejects_bad_requests(eik):
     import torch
     L = eik.lib()
+    w = synth.workload("C2", 24)
+    Fd = torch.from_numpy(w.speed().astype(np.float32)).cuda()
+    out = torch.empty_like(Fd)
+    for kw, code in ((dict(fallback_tau=2.0), eik.EIK_EINVAL), (dict(wait_polls=-1), eik.EIK_EINVAL),
+                     (dict(max_restarts=-5), eik.EIK_EINVAL), (dict(block_dim=16), eik.EIK_ENOTSUP),
+                     (dict(schedule=1), eik.EIK_ENOTSUP), (dict(log_restarts=1), eik.EIK_ENOTSUP)):
+        rc, _ = call(eik, w, Fd, out, 2 * w.h, **kw)
+        assert rc == code, (kw, rc, L.eik_noalloc_last_error())
+    rc, _ = call(eik, w, Fd, out, 0.0)
+    assert rc == eik.EIK_EINVAL
     dims = (256, 256, 128)                      # 32*32*16 = 16384 bricks > 8192
     F = torch.ones((1,), dtype=torch.float32, device="cuda")
     d = (C.c_int32 * 3)(*dims)
