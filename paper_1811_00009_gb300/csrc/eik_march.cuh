@@ -165,9 +165,10 @@ struct BitsOf<double> {
 // (b, c, a) raise gsum everywhere, so hi cannot move up, and if it stays put
 // the distance r2 - gsum(lo) can only shrink and gsum(hi) - r2 only grow
 // (rounded subtraction is monotone), so lo can only become more likely.
-// Searched from the estimate x0.
+// Searched from the estimate x0 (out of line: the estimate is almost always
+// within an ulp of the result, which root_near settles in two evaluations).
 template <typename T>
-__device__ __forceinline__ T root_search(T x0, T a, T b, T c, T r2) {
+__device__ __noinline__ T root_search(T x0, T a, T b, T c, T r2) {
     using U = typename BitsOf<T>::U;
     const U ua = ubits(a);
     U g = ubits(x0);
@@ -226,6 +227,27 @@ __device__ __forceinline__ T root_search(T x0, T a, T b, T c, T r2) {
     return (r2 - glo < ghi - r2) ? from_bits(lo) : from_bits(hi);
 }
 
+// The same root when it lies within an ulp of the estimate x0, which is the
+// usual case: G at x0 says on which side of the crossing x0 lies, G one value
+// further that way closes the bracket.  Otherwise the general search.
+template <typename T>
+__device__ __forceinline__ T root_near(T x0, T a, T b, T c, T r2) {
+    using U = typename BitsOf<T>::U;
+    const U g = ubits(x0);
+    if (g > ubits(a) && g < BitsOf<T>::kInf) {
+        const T g0 = gsum(x0, a, b, c);
+        const bool up = !(g0 >= r2);                 // x0 below the crossing
+        const U g1 = up ? g + 1 : g - 1;
+        const T x1 = from_bits(g1);
+        const T gx1 = gsum(x1, a, b, c);
+        if (up == (gx1 >= r2)) {
+            const T glo = up ? g0 : gx1, ghi = up ? gx1 : g0;
+            return (r2 - glo < ghi - r2) ? (up ? x0 : x1) : (up ? x1 : x0);
+        }
+    }
+    return root_search<T>(x0, a, b, c, r2);
+}
+
 // The estimate (with the causality clamps: in exact arithmetic the root is not
 // below the largest admitted value).  (The division by 3 as a product.)
 __device__ __forceinline__ double root_estimate(double a, double b, double c, double r) {
@@ -242,7 +264,7 @@ __device__ __forceinline__ double root_estimate(double a, double b, double c, do
 }
 
 __device__ __forceinline__ double upwind_root(double a, double b, double c, double r) {
-    return root_search<double>(root_estimate(a, b, c, r), a, b, c, __dmul_rn(r, r));
+    return root_near<double>(root_estimate(a, b, c, r), a, b, c, __dmul_rn(r, r));
 }
 
 // FP32: sqrt(D) as D * rsqrt(D) (the hardware reciprocal square root, a few
@@ -278,7 +300,7 @@ __device__ __forceinline__ float upwind_root_f32(float a, float b, float c, floa
             }
         }
     }
-    return root_search<float>(x, a, b, c, r2);
+    return root_near<float>(x, a, b, c, r2);
 }
 
 // Bounds arrive as doubles; a float node value v satisfies v <= b exactly when
@@ -947,40 +969,46 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
     // masks); none on internal faces of a group, whose neighbours saw them live
     const unsigned U = ((S.upd[pbase >> 5] >> (pbase & 31)) & 0xFFu) |
                        (((S.upd[(pbase + 64) >> 5] >> ((pbase + 64) & 31)) & 0xFFu) << 8);
-    unsigned long long um[6];
-    um[0] = (static_cast<unsigned long long>(U & 1u) << (z0 * 8 + y)) |
-            (static_cast<unsigned long long>((U >> 8) & 1u) << ((z0 + 1) * 8 + y));
-    um[1] = (static_cast<unsigned long long>((U >> 7) & 1u) << (z0 * 8 + y)) |
-            (static_cast<unsigned long long>((U >> 15) & 1u) << ((z0 + 1) * 8 + y));
-    um[2] = (y == 0) ? (static_cast<unsigned long long>(U & 0xFFFFu) << (z0 * 8)) : 0ull;
-    um[3] = (y == 7) ? (static_cast<unsigned long long>(U & 0xFFFFu) << (z0 * 8)) : 0ull;
-    um[4] = (zp == 0) ? (static_cast<unsigned long long>(U & 0xFFu) << (y * 8)) : 0ull;
-    um[5] = (zp == 3) ? (static_cast<unsigned long long>((U >> 8) & 0xFFu) << (y * 8)) : 0ull;
+    unsigned long long um[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+    // A march that lowered no value leaves the brick as its latest copy holds it
+    // (which nodes are accepted follows from the bounds), so it writes nothing:
+    // readers keep taking that copy, and its Upsilon masks, written in an earlier
+    // restart, are not applied again.
+    if (__any_sync(kFull, U != 0u)) {
+        um[0] = (static_cast<unsigned long long>(U & 1u) << (z0 * 8 + y)) |
+                (static_cast<unsigned long long>((U >> 8) & 1u) << ((z0 + 1) * 8 + y));
+        um[1] = (static_cast<unsigned long long>((U >> 7) & 1u) << (z0 * 8 + y)) |
+                (static_cast<unsigned long long>((U >> 15) & 1u) << ((z0 + 1) * 8 + y));
+        um[2] = (y == 0) ? (static_cast<unsigned long long>(U & 0xFFFFu) << (z0 * 8)) : 0ull;
+        um[3] = (y == 7) ? (static_cast<unsigned long long>(U & 0xFFFFu) << (z0 * 8)) : 0ull;
+        um[4] = (zp == 0) ? (static_cast<unsigned long long>(U & 0xFFu) << (y * 8)) : 0ull;
+        um[5] = (zp == 3) ? (static_cast<unsigned long long>((U >> 8) & 0xFFu) << (y * 8)) : 0ull;
 #pragma unroll
-    for (int f = 0; f < 6; ++f) {
-        um[f] = warp_or64(um[f]);
-        if (GROUP && ((gmask >> f) & 1u)) um[f] = 0ull;
-    }
-
-    // ---- write the other copy, then publish it
-    const int ns = (st == kUntouched) ? 0 : (stamp_copy(st) ^ 1);
-    T* dst = P.slot + (static_cast<int64_t>(b) * 2 + ns) * kSlot;
-    {
-        T row[8];
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-#pragma unroll
-            for (int x = 0; x < 8; ++x) row[x] = vabs(S.psi[hbase + 100 * s + x]);
-            store8(dst + pbase + 64 * s, row);
-            dst[kXF0 + (z0 + s) * 8 + y] = row[0];
-            dst[kXF7 + (z0 + s) * 8 + y] = row[7];
+        for (int f = 0; f < 6; ++f) {
+            um[f] = warp_or64(um[f]);
+            if (GROUP && ((gmask >> f) & 1u)) um[f] = 0ull;
         }
+
+        // ---- write the other copy, then publish it
+        const int ns = (st == kUntouched) ? 0 : (stamp_copy(st) ^ 1);
+        T* dst = P.slot + (static_cast<int64_t>(b) * 2 + ns) * kSlot;
+        {
+            T row[8];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+#pragma unroll
+                for (int x = 0; x < 8; ++x) row[x] = vabs(S.psi[hbase + 100 * s + x]);
+                store8(dst + pbase + 64 * s, row);
+                dst[kXF0 + (z0 + s) * 8 + y] = row[0];
+                dst[kXF7 + (z0 + s) * 8 + y] = row[7];
+            }
+        }
+        if (lane < 6) P.ups[(static_cast<int64_t>(b) * 2 + ns) * 6 + lane] = um[lane];
+        // No fence: nobody reads this copy before the grid barrier that ends the
+        // restart (a reader that sees the new stamp takes the other copy).
+        if (lane == 0)
+            P.stamp[b] = make_stamp(k, st == kUntouched ? static_cast<int>(kNever) : stamp_latest(st), ns);
     }
-    if (lane < 6) P.ups[(static_cast<int64_t>(b) * 2 + ns) * 6 + lane] = um[lane];
-    // No fence: nobody reads this copy before the grid barrier that ends the
-    // restart (a reader that sees the new stamp takes the other copy).
-    if (lane == 0)
-        P.stamp[b] = make_stamp(k, st == kUntouched ? static_cast<int>(kNever) : stamp_latest(st), ns);
 
     // ---- activation for restart k+1 (A of Alg. 4/5, C of Alg. 4)
     // (once the bound has reached width_band, pending nodes above it stay tentative: Alg. 6's A flag)
