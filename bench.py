@@ -157,22 +157,39 @@ def cpu_oracle_sample(n: int, seed_cfg: str = "C4"):
     return w, F, psi, dt
 
 
-def cpu_block_sample(n: int):
-    """Time the CPU form of the paper's method (Alg. 6, OpenMP over blocks, FP64) on all host cores,
-    block edge 32 and stride 2h (the paper's parallel optimum), on the workload family at n^3."""
+def cpu_block_sample(w, F):
+    """Time the CPU form of the paper's method (the oracle's Alg. 6, OpenMP over blocks, FP64) on all host
+    cores, block edge 32 and stride 2h (the paper's parallel optimum), on workload w with speeds F (host,
+    float64).  Returns the baseline record and the oracle's psi (the oracle tests pin the block solver to the
+    single-heap one: identical with one block, equal to machine accuracy with many)."""
     import oracle
-    import synth
-    w = synth.workload("C4", n)
-    F = w.speed()
     oracle.build()
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    _, st = oracle.block_fmm(F, w.h, w.sources, 32, 2.0 * w.h, nthreads=cores)
+    psi, st = oracle.block_fmm(F, w.h, w.sources, 32, 2.0 * w.h, nthreads=cores)
     dt = time.perf_counter() - t0
+    n = w.dims[0]
     return {"value": w.npoints / dt / 1e6, "unit": "Mpoints/s", "cores": cores,
             "kind": "oracle block solver (Alg. 6 with OpenMP)",
-            "sample": f"one full solve of the C4 family at {n}^3, block 32, stride 2h, FP64, {dt:.2f} s, "
-                      f"{st['nr']} restarts"}
+            "sample": f"one full solve of the benchmark's workload ({n}^3, the same F), block 32, stride 2h, FP64, "
+                      f"{dt:.2f} s, {st['nr']} restarts"}, psi
+
+
+def max_abs_error(psi32, ref) -> float:
+    """max |psi - ref| over the finite nodes of ref, in chunks (the full-size arrays are GiB-sized);
+    inf if the sets of unreachable nodes differ."""
+    import numpy as np
+    a, b = psi32.reshape(-1), ref.reshape(-1)
+    err = 0.0
+    step = 1 << 26
+    for lo in range(0, a.size, step):
+        x, y = a[lo:lo + step].astype(np.float64), b[lo:lo + step]
+        m = np.isfinite(y)
+        if not np.array_equal(np.isfinite(x), m):
+            return float("inf")
+        if m.any():
+            err = max(err, float(np.max(np.abs(x[m] - y[m]))))
+    return err
 
 
 def run_reference(args):
@@ -303,16 +320,6 @@ def run_ours(args):
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
 
-    # CPU baseline first (rank 0, N = 1), before the GPU work starts
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        w_s, F_s, psi_s, dt = cpu_oracle_sample(args.cpu_n)
-        cpu = {"value": w_s.npoints / dt / 1e6, "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
-               "sample": f"one full solve of the C4 family at {args.cpu_n}^3 (same F recipe, h=1/{args.cpu_n - 1}, "
-                         f"centre source) by the single-heap FP64 fast marching oracle, one thread, {dt:.1f} s"}
-        if args.cpu_block_n:
-            cpu["block_solver"] = cpu_block_sample(args.cpu_block_n)
-
     import __graft_entry__
     __graft_entry__.build()
     import paper_1811_00009_gb300 as eik
@@ -324,6 +331,19 @@ def run_ours(args):
     Fd = w.speed_torch(dev)
     if prec == "fp64":
         Fd = Fd.double()
+
+    # CPU baseline first (rank 0, N = 1), before the timed GPU work: the single-heap oracle on one core on a
+    # 160^3 sample of the family, and the oracle's block solver on every host core on the benchmark's own
+    # workload (the same F), whose result also gives the element-wise error of the timed solve at full size
+    cpu = None
+    full_ref = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        w_s, F_s, psi_s, dt = cpu_oracle_sample(args.cpu_n)
+        cpu = {"value": w_s.npoints / dt / 1e6, "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
+               "sample": f"one full solve of the C4 family at {args.cpu_n}^3 (same F recipe, h=1/{args.cpu_n - 1}, "
+                         f"centre source) by the single-heap FP64 fast marching oracle, one thread, {dt:.1f} s"}
+        if not args.no_cpu_block:
+            cpu["block_solver"], full_ref = cpu_block_sample(w, Fd.double().cpu().numpy())
     ctx = eik.eik_create(w.dims, w.h, Fd, prec)
     eik.eik_add_sources(ctx, w.sources)
     stride = args.stride_h * w.h
@@ -443,8 +463,20 @@ def run_ours(args):
                "step_ms_median": float(np.median(gaps)) if len(gaps) else None,
                "last_copy_ms": (t1 - marks[-1]) * 1e3 if marks else None}
 
-    # accuracy of this run's path against the FP64 oracle on the CPU-baseline sample
+    # accuracy of this run's path against the FP64 oracle: the timed solve itself, every node, against the
+    # block oracle at full size; and the same path on the single-heap oracle's 160^3 sample
     err = None
+    if full_ref is not None:
+        o = torch.empty_like(Fd)
+        eik.eik_result(ctx, o)
+        torch.cuda.synchronize()
+        e_full = max_abs_error(o.cpu().numpy(), full_ref)
+        top = float(np.max(full_ref[np.isfinite(full_ref)]))
+        del o
+        err = {"max_abs_over_max_psi": e_full / top, "grid": [n, n, n], "nodes": "every node",
+               "oracle": "block solver (Alg. 6, FP64, OpenMP), pinned to the single-heap oracle",
+               "tolerance": 1e-5 if prec == "fp32" else None}
+        full_ref = None
     if cpu is not None:
         Fs = torch.from_numpy(F_s.astype(np.float32 if prec == "fp32" else np.float64)).to(dev)
         c2 = eik.eik_create(w_s.dims, w_s.h, Fs, prec)
@@ -457,10 +489,32 @@ def run_ours(args):
         eik.eik_destroy(c2)
         p = o.double().cpu().numpy()
         fin = np.isfinite(psi_s)
-        err = {"max_abs_over_max_psi": float(np.max(np.abs(p[fin] - psi_s[fin])) / psi_s[fin].max()),
-               "grid": [args.cpu_n] * 3, "tolerance": 1e-5 if prec == "fp32" else None}
+        small = {"max_abs_over_max_psi": float(np.max(np.abs(p[fin] - psi_s[fin])) / psi_s[fin].max()),
+                 "grid": [args.cpu_n] * 3, "oracle": "single-heap FMM (Algs. 1-4, FP64)",
+                 "tolerance": 1e-5 if prec == "fp32" else None}
+        if err is None:
+            err = small
+        else:
+            err["sample_single_heap"] = small
 
     eik.eik_destroy(ctx)
+    # the FP64 production variant of the whole pipeline on the same workload (one warm-up, one timed solve)
+    fp64 = None
+    if not args.no_fp64 and prec == "fp32" and rank == 0:
+        F64 = Fd.double()
+        c64 = eik.eik_create(w.dims, w.h, F64, "fp64")
+        eik.eik_add_sources(c64, w.sources)
+        eik.eik_solve_ex(c64, 2.0 * w.h)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)                # torch creates the CUDA events on first record; the library re-records them
+        e1.record(stream)
+        st64 = eik.eik_solve_ex(c64, 2.0 * w.h, loop_events=(e0, e1))
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        eik.eik_destroy(c64)
+        del F64
+        fp64 = {"mpoints_per_s": w.npoints / (ms64 * 1e-3) / 1e6, "loop_ms": ms64, "restarts": st64["restarts"],
+                "config": "FP64 storage and arithmetic, fixed stride 2h, 8^3 blocks, same workload"}
     batch = None
     if not args.no_batch and rank == 0:
         batch = batch_bench(eik, synth, args.batch_steps, 3, args.tune_rounds, dev)
@@ -493,7 +547,7 @@ def run_ours(args):
             "solve": {"restarts": s0["restarts"], "marches": s0["marches"], "accepted": s0["accepted"],
                       "solves": s0["solves"], "updates": s0["updates"], "fallbacks": s0["fallbacks"],
                       "rounds": s0["rounds"], "loop_ms": loop_avg_ms},
-            "error_vs_oracle": err, "batch": batch}
+            "error_vs_oracle": err, "fp64_solve": fp64, "batch": batch}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -513,7 +567,9 @@ def main():
     ap.add_argument("--schedule", choices=["learned", "fixed"], default="learned")
     ap.add_argument("--window", type=float, default=0.0)
     ap.add_argument("--cpu-n", type=int, default=160)
-    ap.add_argument("--cpu-block-n", type=int, default=256, help="grid edge of the multi-core CPU block-solver sample (0: skip)")
+    ap.add_argument("--no-cpu-block", action="store_true",
+                    help="skip the multi-core CPU block solver on the full workload (and the full-size error)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 solve of the same workload")
     ap.add_argument("--ref-n", type=int, default=128)
     ap.add_argument("--e2e-steps", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -273,11 +273,20 @@ __device__ __forceinline__ double upwind_root(double a, double b, double c, doub
 // root is taken in double precision and rounded (rounding is monotone too).
 __device__ __forceinline__ float sqrt_f32(float D) { return D * rsqrtf(fmaxf(D, FLT_MIN)); }
 
+// (the double-precision paths out of line: they almost never run, and inlined
+// they would crowd the instruction cache around the hot solve loop)
+static __device__ __noinline__ float root_in_double(float a, float b, float c, float r) {
+    return static_cast<float>(upwind_root(a, b, c, r));
+}
+static __device__ __noinline__ float estimate_in_double(float a, float b, float c, float r) {
+    return static_cast<float>(root_estimate(a, b, c, r));
+}
+
 __device__ __forceinline__ float upwind_root_f32(float a, float b, float c, float r, float tau, int& fb) {
     const float r2 = __fmul_rn(r, r);
     if (!(r2 >= FLT_MIN)) {
         ++fb;
-        return static_cast<float>(upwind_root(a, b, c, r));
+        return root_in_double(a, b, c, r);
     }
     float x = a + r;
     if (x > b) {
@@ -285,7 +294,7 @@ __device__ __forceinline__ float upwind_root_f32(float a, float b, float c, floa
         float D = 2.0f * r2 - d * d;
         if (!(D >= tau * 2.0f * r2)) {
             ++fb;
-            x = static_cast<float>(root_estimate(a, b, c, r));
+            x = estimate_in_double(a, b, c, r);
         } else {
             x = fmaxf(a + (d + sqrt_f32(D)) * 0.5f, b);
             if (x > c) {
@@ -293,7 +302,7 @@ __device__ __forceinline__ float upwind_root_f32(float a, float b, float c, floa
                 D = 3.0f * r2 - (d * d + e * e + g * g);
                 if (!(D >= tau * 3.0f * r2)) {
                     ++fb;
-                    x = static_cast<float>(root_estimate(a, b, c, r));
+                    x = estimate_in_double(a, b, c, r);
                 } else {
                     x = fmaxf(a + (d + e + sqrt_f32(D)) * (1.0f / 3.0f), c);
                 }
