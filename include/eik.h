@@ -281,6 +281,47 @@ const char *eik_last_error(const eik_ctx *ctx);
 const char *eik_version(void);
 
 /*
+ * One grid sharded across GPUs.  The blocks of Sec. 2.3 are cut into slabs of
+ * whole 8^3-brick planes along z, one slab per GPU.  Each GPU holds its slab
+ * plus one ghost brick plane beyond each cut (a context over that extended
+ * part of the grid: node planes [z_lo, z_hi) of the full grid, with the
+ * sources in its own coordinates).  The restarts of Alg. 6 run in lockstep:
+ * every GPU marches its own active bricks up to the same bound (bound_k is
+ * preset by the stride, so it needs no exchange), then each cut's face layers
+ * go to the GPU across it and are merged into its ghost plane (Alg. 5 across
+ * the cut; a lowered face puts the adjacent brick on the next restart's list),
+ * and the solve ends when no GPU has a brick listed.  The result is the same,
+ * bit for bit, as one GPU's: the update is monotone, so the order of work does
+ * not change the fixed point.  Every call waits for its work.
+ *
+ * eik_slab_set      mark brick planes [own_bz0, own_bz1) of ctx's grid as this
+ *                   GPU's (0 <= own_bz0 < own_bz1 <= ceil(nz/8)); the planes
+ *                   outside are ghosts, never marched here.
+ * eik_slab_begin    Alg. 1 and the work list of restart 1 (sources as added
+ *                   with eik_add_sources), fixed stride (finite, > 0), 8^3 blocks.
+ * eik_slab_restart  one restart on this GPU; *pending (nullable) = bricks on
+ *                   the next restart's list so far.
+ * eik_slab_export   side 0: the z = 0 face layer of plane own_bz0 (for the GPU
+ *                   below); side 1: the z = 7 face layer of plane own_bz1 - 1
+ *                   (for the GPU above); into buf, DEVICE memory of
+ *                   eik_slab_face_bytes(ctx) bytes owned by the caller.
+ * eik_slab_import   the record the GPU across side exported (side 0: below,
+ *                   into ghost plane own_bz0 - 1; side 1: above, into plane
+ *                   own_bz1), DEVICE memory; *pending as above, imports counted.
+ * eik_slab_end      finish (the psi of the own planes is then read with
+ *                   eik_result, whose ghost planes hold no meaningful values).
+ * Errors: EIK_EINVAL (planes, side, buffers, stride), EIK_ESTATE (order of
+ * calls), EIK_ETIMEOUT (a device wait limit or the restart cap), EIK_ECUDA.
+ */
+int64_t eik_slab_face_bytes(const eik_ctx *ctx);
+eik_status eik_slab_set(eik_ctx *ctx, int32_t own_bz0, int32_t own_bz1);
+eik_status eik_slab_begin(eik_ctx *ctx, double stride);
+eik_status eik_slab_restart(eik_ctx *ctx, int64_t *pending);
+eik_status eik_slab_export(eik_ctx *ctx, int32_t side, void *buf);
+eik_status eik_slab_import(eik_ctx *ctx, int32_t side, const void *buf, int64_t *pending);
+eik_status eik_slab_end(eik_ctx *ctx, eik_stats *stats);
+
+/*
  * Restart-schedule network (no counterpart in the paper; the paper fixes the
  * stride).  A multilayer perceptron EIK_SCHED_INPUTS -> EIK_SCHED_HIDDEN (tanh)
  * -> EIK_SCHED_HIDDEN (tanh) -> EIK_SCHED_ACTIONS maps the front statistics of
@@ -416,13 +457,18 @@ eik_status eik_batch_result(eik_batch *b, int32_t i, void *psi_out, int out_on_d
 /*
  * eik_batch_autotune -- pick the tiles and CTAs per SM of this batch by timing
  * it on the device (each run is a full eik_batch_solve).  Candidates: stride of
- * grid s = c * h_s with c in {1.5, 2, 2.5, 3, 4}, or f * edge_s * rmin_s with
+ * grid s = c * h_s with c in {1.25, 1.5, 1.75, 2, 2.5, 3, 4}, or f * edge_s * rmin_s with
  * f in {0.5, 0.75, 1, 1.5, 2} (rmin_s = min h/F), block edge 16 for the grids
  * with at least m bricks, m in {never, 2048, 512, 0}, and every CTAs-per-SM
  * count that fits.  Search:
  * successive halving -- time every candidate once, keep the best third, time
  * the survivors twice as often, and so on until one is left (at most `rounds`
- * rounds; 0 = no limit).  The winner is kept in the batch for later solves
+ * rounds; 0 = no limit).  A second stage then tiles grid by grid: the grids
+ * that finish last under the winner (done_ms at or above the 50/75/90 %
+ * quantile) get a stride 1.25, 1.5 or 2 times longer, or those that finish
+ * first (at or below the 25/50/75 % quantile) one 0.5 or 0.75 times as long,
+ * and the same halving picks among these fifteen and the winner.  The result
+ * is kept in the batch for later solves
  * given tiles = NULL and ctas_per_sm = 0, and returned in tiles_out (n tiles,
  * nullable), ctas_per_sm (nullable) and best_ms (its median device time,
  * nullable).  The batch's psi afterwards is that of the last timed run.

@@ -790,7 +790,7 @@ std::vector<eik_batch_tile> tiles_of(const eik_batch* b, const Cand& c) {
 template <typename T>
 eik_status autotune(eik_batch* b, int32_t rounds_cap, eik_batch_tile* tiles_out, int32_t* ctas_out, double* ms_out) {
     const double factors[] = {0.5, 0.75, 1.0, 1.5, 2.0};
-    const double per_h[] = {1.5, 2.0, 2.5, 3.0, 4.0};
+    const double per_h[] = {1.25, 1.5, 1.75, 2.0, 2.5, 3.0, 4.0};
     const int64_t min16s[] = {INT64_MAX, 2048, 512, 0};
     std::vector<Cand> cands;
     for (int c = b->per_sm_max; c >= 1; --c)                 // the default tiles (8^3, 2h, all CTAs) first
@@ -847,20 +847,97 @@ eik_status autotune(eik_batch* b, int32_t rounds_cap, eik_batch_tile* tiles_out,
         reps *= 2;
         ++round;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (st != EIK_OK) return st;
-    if (alive.empty()) return bfail(b, EIK_ETIMEOUT, "eik_batch_autotune: every candidate hit a cap");
+    if (st != EIK_OK || alive.empty()) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (st != EIK_OK) return st;
+        return bfail(b, EIK_ETIMEOUT, "eik_batch_autotune: every candidate hit a cap");
+    }
     std::sort(alive.begin(), alive.end(), [](const Score& x, const Score& y) {
         if (x.ms.empty() != y.ms.empty()) return !x.ms.empty();
         return !x.ms.empty() && x.med() < y.med();
     });
     const Cand& best = cands[alive[0].idx];
-    b->tuned = tiles_of(b, best);
+    std::vector<eik_batch_tile> win = tiles_of(b, best);
+    float win_ms = alive[0].ms.empty() ? 0.0f : alive[0].med();
+
+    // Stage 2, per grid: the launch lasts as long as its slowest grids.  The
+    // grids that finish last under the stage-1 tiles (done_ms at or above a
+    // quantile q of the grids) get a stride longer by a factor (fewer restarts
+    // for them); or the grids that finish first (done_ms at or below q) get a
+    // shorter one (less refresh work in the restarts all grids share, more
+    // restarts for grids that are not the last to finish).  Candidates q x
+    // factor, timed with the same successive halving against the stage-1 tiles.
+    {
+        float ms = 0.0f;
+        st = batch_run_timed<T>(b, win, best.ctas, P, e0, e1, &ms);
+        std::vector<eik_batch_solve_info> info(b->n);
+        if (st == EIK_OK) st = eik_batch_info(b, info.data(), b->n);
+        if (st == EIK_OK) {
+            std::vector<double> done(b->n);
+            for (int i = 0; i < b->n; ++i) done[i] = info[i].done_ms;
+            std::vector<double> sorted = done;
+            std::sort(sorted.begin(), sorted.end());
+            std::vector<std::vector<eik_batch_tile>> tl{win};
+            for (double q : {0.5, 0.75, 0.9})
+                for (double f : {1.25, 1.5, 2.0}) {
+                    const double thr = sorted[static_cast<size_t>(q * (b->n - 1))];
+                    std::vector<eik_batch_tile> t = win;
+                    for (int i = 0; i < b->n; ++i)
+                        if (done[i] >= thr) t[i].stride *= f;
+                    tl.push_back(t);
+                }
+            for (double q : {0.25, 0.5, 0.75})
+                for (double f : {0.5, 0.75}) {
+                    const double thr = sorted[static_cast<size_t>(q * (b->n - 1))];
+                    std::vector<eik_batch_tile> t = win;
+                    for (int i = 0; i < b->n; ++i)
+                        if (done[i] <= thr) t[i].stride *= f;
+                    tl.push_back(t);
+                }
+            std::vector<Score> alive2;
+            for (size_t i = 0; i < tl.size(); ++i) alive2.push_back(Score{i, {}});
+            int reps2 = 1, round2 = 0;
+            while (st == EIK_OK && alive2.size() > 1 && (rounds_cap <= 0 || round2 < rounds_cap)) {
+                std::vector<Score> next;
+                for (auto& a : alive2) {
+                    bool ok = true;
+                    for (int r = 0; r < reps2 && ok; ++r) {
+                        float m2 = 0.0f;
+                        const eik_status s1 = batch_run_timed<T>(b, tl[a.idx], best.ctas, P, e0, e1, &m2);
+                        if (s1 == EIK_ETIMEOUT) ok = false;
+                        else if (s1 != EIK_OK) {
+                            st = s1;
+                            ok = false;
+                        } else {
+                            a.ms.push_back(m2);
+                        }
+                    }
+                    if (st != EIK_OK) break;
+                    if (ok) next.push_back(a);
+                }
+                if (st != EIK_OK) break;
+                std::sort(next.begin(), next.end(), [](const Score& x, const Score& y) { return x.med() < y.med(); });
+                next.resize(std::max<size_t>(1, (next.size() + 2) / 3));
+                alive2.swap(next);
+                reps2 *= 2;
+                ++round2;
+            }
+            if (st == EIK_OK && !alive2.empty() && !alive2[0].ms.empty()) {
+                std::sort(alive2.begin(), alive2.end(), [](const Score& x, const Score& y) { return x.med() < y.med(); });
+                win = tl[alive2[0].idx];
+                win_ms = alive2[0].med();
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != EIK_OK) return st;
+    b->tuned = win;
     b->tuned_ctas = best.ctas;
     if (tiles_out) std::copy(b->tuned.begin(), b->tuned.end(), tiles_out);
     if (ctas_out) *ctas_out = best.ctas;
-    if (ms_out) *ms_out = alive[0].ms.empty() ? 0.0 : static_cast<double>(alive[0].med());
+    if (ms_out) *ms_out = static_cast<double>(win_ms);
     return EIK_OK;
 }
 
