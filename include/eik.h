@@ -284,8 +284,7 @@ const char *eik_version(void);
  * One grid sharded across GPUs.  The blocks of Sec. 2.3 are cut into slabs of
  * whole 8^3-brick planes along z, one slab per GPU.  Each GPU holds its slab
  * plus one ghost brick plane beyond each cut (a context over that extended
- * part of the grid: node planes [z_lo, z_hi) of the full grid, with the
- * sources in its own coordinates).  The restarts of Alg. 6 run in lockstep:
+ * part of the grid: node planes [z_lo, z_hi) of the full grid).  The restarts of Alg. 6 run in lockstep:
  * every GPU marches its own active bricks up to the same bound (bound_k is
  * preset by the stride, so it needs no exchange), then each cut's face layers
  * go to the GPU across it and are merged into its ghost plane (Alg. 5 across
@@ -294,11 +293,17 @@ const char *eik_version(void);
  * bit for bit, as one GPU's: the update is monotone, so the order of work does
  * not change the fixed point.  Every call waits for its work.
  *
- * eik_slab_set      mark brick planes [own_bz0, own_bz1) of ctx's grid as this
- *                   GPU's (0 <= own_bz0 < own_bz1 <= ceil(nz/8)); the planes
- *                   outside are ghosts, never marched here.
+ * eik_slab_set      ctx's grid is node planes [zoff, zoff + nz) of a grid of
+ *                   nz_all planes (zoff a multiple of 8); mark its brick planes
+ *                   [own_bz0, own_bz1) as this GPU's (0 <= own_bz0 < own_bz1 <=
+ *                   ceil(nz/8)); the planes outside are ghosts, never marched
+ *                   here.  Call it before eik_add_sources: the sources are then
+ *                   given in the whole grid's coordinates (z in [0, (nz_all-1)h]),
+ *                   and every part computes psi0 at its fixed nodes exactly as
+ *                   one grid would.
  * eik_slab_begin    Alg. 1 and the work list of restart 1 (sources as added
- *                   with eik_add_sources), fixed stride (finite, > 0), 8^3 blocks.
+ *                   with eik_add_sources, possibly none on this GPU), fixed
+ *                   stride (finite, > 0), 8^3 blocks.
  * eik_slab_restart  one restart on this GPU; *pending (nullable) = bricks on
  *                   the next restart's list so far.
  * eik_slab_export   side 0: the z = 0 face layer of plane own_bz0 (for the GPU
@@ -314,7 +319,7 @@ const char *eik_version(void);
  * calls), EIK_ETIMEOUT (a device wait limit or the restart cap), EIK_ECUDA.
  */
 int64_t eik_slab_face_bytes(const eik_ctx *ctx);
-eik_status eik_slab_set(eik_ctx *ctx, int32_t own_bz0, int32_t own_bz1);
+eik_status eik_slab_set(eik_ctx *ctx, int32_t own_bz0, int32_t own_bz1, int32_t zoff, int32_t nz_all);
 eik_status eik_slab_begin(eik_ctx *ctx, double stride);
 eik_status eik_slab_restart(eik_ctx *ctx, int64_t *pending);
 eik_status eik_slab_export(eik_ctx *ctx, int32_t side, void *buf);

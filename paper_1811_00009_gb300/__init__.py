@@ -129,6 +129,20 @@ def lib():
             L.eik_solve_async.argtypes = [vp, C.POINTER(eik_params)]
             L.eik_wait.restype = i32
             L.eik_wait.argtypes = [vp, C.POINTER(eik_stats)]
+            L.eik_slab_face_bytes.restype = i64
+            L.eik_slab_face_bytes.argtypes = [vp]
+            L.eik_slab_set.restype = i32
+            L.eik_slab_set.argtypes = [vp, i32, i32, i32, i32]
+            L.eik_slab_begin.restype = i32
+            L.eik_slab_begin.argtypes = [vp, dbl]
+            L.eik_slab_restart.restype = i32
+            L.eik_slab_restart.argtypes = [vp, C.POINTER(i64)]
+            L.eik_slab_export.restype = i32
+            L.eik_slab_export.argtypes = [vp, i32, vp]
+            L.eik_slab_import.restype = i32
+            L.eik_slab_import.argtypes = [vp, i32, vp, C.POINTER(i64)]
+            L.eik_slab_end.restype = i32
+            L.eik_slab_end.argtypes = [vp, C.POINTER(eik_stats)]
             L.eik_autotune.restype = i32
             L.eik_autotune.argtypes = [vp, i32, C.POINTER(dbl), C.POINTER(i32), C.POINTER(dbl)]
             L.eik_restart_log.restype = i32
@@ -340,6 +354,41 @@ def eik_autotune(ctx, rounds: int = 0) -> Dict[str, Any]:
     stride, block, ms = C.c_double(), C.c_int32(), C.c_double()
     _check(lib().eik_autotune(ctx, int(rounds), C.byref(stride), C.byref(block), C.byref(ms)), ctx)
     return {"stride": stride.value, "block_dim": block.value, "ms": ms.value}
+
+
+def eik_slab_face_bytes(ctx) -> int:
+    return int(lib().eik_slab_face_bytes(ctx))
+
+
+def eik_slab_set(ctx, own_bz0: int, own_bz1: int, zoff: int, nz_all: int) -> None:
+    _check(lib().eik_slab_set(ctx, int(own_bz0), int(own_bz1), int(zoff), int(nz_all)), ctx)
+
+
+def eik_slab_begin(ctx, stride: float) -> None:
+    _check(lib().eik_slab_begin(ctx, float(stride)), ctx)
+
+
+def eik_slab_restart(ctx) -> int:
+    n = C.c_int64()
+    _check(lib().eik_slab_restart(ctx, C.byref(n)), ctx)
+    return n.value
+
+
+def eik_slab_export(ctx, side: int, buf) -> None:
+    """buf: a torch CUDA tensor of eik_slab_face_bytes(ctx) bytes."""
+    _check(lib().eik_slab_export(ctx, int(side), _dptr(buf)), ctx)
+
+
+def eik_slab_import(ctx, side: int, buf) -> int:
+    n = C.c_int64()
+    _check(lib().eik_slab_import(ctx, int(side), _dptr(buf), C.byref(n)), ctx)
+    return n.value
+
+
+def eik_slab_end(ctx) -> Dict[str, Any]:
+    s = eik_stats()
+    _check(lib().eik_slab_end(ctx, C.byref(s)), ctx)
+    return _stats_dict(s)
 
 
 def eik_restart_log(ctx, cap: int = 1 << 16) -> List[Dict[str, Any]]:

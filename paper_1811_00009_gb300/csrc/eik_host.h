@@ -41,9 +41,13 @@ struct Cand {
 
 // Every node of every cell that contains a source (xyz: n*3 coordinates), into
 // out[0 .. 8*nsrc); returns the count.  (Fixed-size arrays: the allocation-free
-// entry point uses these forms directly.)
+// entry point uses these forms directly.)  A part of a grid sharded in z holds
+// node planes [zoff, zoff + nz_part) of a grid of nz planes: the sources and
+// the distances stay in the whole grid's coordinates (so every part computes
+// the same psi0 as one grid would), and nodes outside the part are dropped.
 inline int source_candidates_into(const double* xyz, int nsrc, int nx, int ny, int nz, double h, const Bricks& g,
-                                  Cand* out) {
+                                  Cand* out, int zoff = 0, int nz_part = -1) {
+    if (nz_part < 0) nz_part = nz;
     int n = 0;
     for (int q = 0; q < nsrc; ++q) {
         const double* xs = xyz + 3 * q;
@@ -55,10 +59,12 @@ inline int source_candidates_into(const double* xyz, int nsrc, int nx, int ny, i
             for (int bq = 0; bq < cn[1]; ++bq)
                 for (int d = 0; d < cn[0]; ++d) {
                     const int i = ci[0][d], j = ci[1][bq], k = ci[2][a];
+                    const int kl = k - zoff;
+                    if (kl < 0 || kl >= nz_part) continue;
                     const double dx = i * h - xs[0], dy = j * h - xs[1], dz = k * h - xs[2];
                     Cand c;
-                    c.b = g.boff + ((k >> 3) * g.BY + (j >> 3)) * g.BX + (i >> 3);
-                    c.p = ((k & 7) * 8 + (j & 7)) * 8 + (i & 7);
+                    c.b = g.boff + ((kl >> 3) * g.BY + (j >> 3)) * g.BX + (i >> 3);
+                    c.p = ((kl & 7) * 8 + (j & 7)) * 8 + (i & 7);
                     c.dist = std::sqrt(dx * dx + dy * dy + dz * dz);
                     out[n++] = c;
                 }
@@ -67,10 +73,10 @@ inline int source_candidates_into(const double* xyz, int nsrc, int nx, int ny, i
 }
 
 inline void source_candidates(const double* xyz, int nsrc, int nx, int ny, int nz, double h, const Bricks& g,
-                              std::vector<Cand>& out) {
+                              std::vector<Cand>& out, int zoff = 0, int nz_part = -1) {
     const size_t at = out.size();
     out.resize(at + 8 * static_cast<size_t>(nsrc > 0 ? nsrc : 0));
-    const int n = source_candidates_into(xyz, nsrc, nx, ny, nz, h, g, out.data() + at);
+    const int n = source_candidates_into(xyz, nsrc, nx, ny, nz, h, g, out.data() + at, zoff, nz_part);
     out.resize(at + n);
 }
 

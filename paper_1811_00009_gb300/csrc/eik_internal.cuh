@@ -107,6 +107,17 @@ struct RestartRec {            // mirrors eik_restart_rec
     float features[10];
 };
 
+// A brick's face as a neighbouring GPU exports it (a grid sharded in z): the 64
+// values of the face layer of the brick's latest copy, the Upsilon mask of
+// that copy on that face, and the restart that wrote it (-1: untouched).
+template <typename T>
+struct FaceRec {
+    T v[64];
+    unsigned long long ups;
+    int32_t written;
+    int32_t pad;
+};
+
 // One grid of a batched launch: its place in the launch's brick and group
 // index spaces, its block edge and its stride (bound of restart k = k*stride).
 struct SolveDesc {
@@ -137,6 +148,9 @@ struct LoopParams {
     int32_t* qgroup;           // kRing x ngroups, as queued
     int32_t* glist[kRing];     // group work lists by ring slot
     int32_t early;             // non-zero: waiting warps may march the next restart's bricks early
+    int32_t own_bz0, own_bz1;  // brick planes (z) this launch owns: bricks outside are ghosts of a grid
+                               // sharded across GPUs (their faces are imported; never put on a work list)
+    int32_t pause;             // non-zero: stop after every restart (the sharded solve exchanges faces)
     double width;              // width_band of Alg. 6 (+inf: the full solve)
     Ctrl* ctrl;
     RestartRec* log;

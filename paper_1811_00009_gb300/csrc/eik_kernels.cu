@@ -182,7 +182,7 @@ __device__ void restart_end(const LoopParams<T>& P, int lane, float* scratch) {
     C->head[s] = 0;
     C->gcount[s] = 0;
     C->ghead[s] = 0;
-    if (n_next == 0 || (__ldcg(&C->status) & kStWaitTimeout)) {
+    if ((n_next == 0 && !P.pause) || (__ldcg(&C->status) & kStWaitTimeout)) {
         // (no work left, or a wait somewhere ran out: no warp starts another restart)
         C->done = 1;
         C->t_end = now;
@@ -191,6 +191,12 @@ __device__ void restart_end(const LoopParams<T>& P, int lane, float* scratch) {
         C->status |= kStRestartCap;
         C->t_end = now;
     } else {
+        // (a sharded grid pauses after every restart, its state set up for the next one: the host
+        // imports the neighbours' faces, which may list more bricks, and decides whether to go on)
+        if (P.pause) {
+            C->done = 1;
+            C->t_end = now;
+        }
         const double bnd = __ldcg(&C->bound);
         C->k = k + 1;
         C->mode = next_mode;
@@ -501,6 +507,62 @@ __global__ void k_result(const T* __restrict__ slot, const unsigned long long* _
     }
 }
 
+// A grid sharded in z across GPUs: the face layer of every brick of plane bz
+// that a neighbouring GPU's bricks read (face 4: the z = 0 layer, read by the
+// GPU below; face 5: the z = 7 layer, read by the GPU above), with the Upsilon
+// mask of the brick's latest copy on that face.  One CTA of 64 threads per brick.
+template <typename T>
+__global__ void k_slab_export(const T* __restrict__ slot, const unsigned long long* __restrict__ ups,
+                              const unsigned long long* __restrict__ stamp, int BX, int BY, int bz, int face,
+                              FaceRec<T>* __restrict__ out) {
+    const int bxy = blockIdx.x, t = threadIdx.x;
+    const int64_t b = static_cast<int64_t>(bz) * BX * BY + bxy;
+    const unsigned long long st = stamp[b];
+    FaceRec<T>& R = out[bxy];
+    if (st == kUntouched) {
+        R.v[t] = Num<T>::inf();
+        if (t == 0) {
+            R.ups = 0ull;
+            R.written = -1;
+        }
+        return;
+    }
+    const int64_t c = b * 2 + stamp_copy(st);
+    R.v[t] = slot[c * kSlot + (face == 4 ? t : 7 * 64 + t)];
+    if (t == 0) {
+        R.ups = ups[c * 6 + face];
+        R.written = stamp_latest(st);
+    }
+}
+
+// The faces a neighbouring GPU exported -> the ghost plane gbz of this GPU's
+// part of the grid (copy 0 of each ghost brick: the layer this GPU's bricks
+// read, the Upsilon mask on that face, the stamp), after the restart k_done.
+// A ghost face lowered in that restart puts the adjacent brick of plane obz on
+// the work list of restart k_done + 1 (C of Alg. 4 across the GPUs' cut).
+template <typename T>
+__global__ void k_slab_import(T* __restrict__ slot, unsigned long long* __restrict__ ups,
+                              unsigned long long* __restrict__ stamp, int BX, int BY, int gbz, int obz,
+                              const FaceRec<T>* __restrict__ in, int k_done, int32_t* queued, int64_t nbricks,
+                              Ctrl* C, int32_t* list_next) {
+    const int bxy = blockIdx.x, t = threadIdx.x;
+    const int64_t g = static_cast<int64_t>(gbz) * BX * BY + bxy;
+    const FaceRec<T>& R = in[bxy];
+    const bool below = gbz < obz;      // the ghost plane under this GPU's bricks: they read its z = 7 layer
+    slot[g * 2 * kSlot + (below ? 7 * 64 + t : t)] = R.v[t];
+    if (t != 0) return;
+    ups[g * 2 * 6 + (below ? 5 : 4)] = R.ups;
+    stamp[g] = (R.written < 0) ? kUntouched : make_stamp(R.written, static_cast<int>(kNever), 0);
+    if (R.ups != 0ull && R.written == k_done) {
+        const int k_next = k_done + 1, s = k_next % kRing;
+        const int32_t x = static_cast<int32_t>(static_cast<int64_t>(obz) * BX * BY + bxy);
+        if (atomicMax(queued + s * nbricks + x, k_next) < k_next) {
+            const int pos = atomicAdd(&C->count[s], 1);
+            list_next[pos] = x;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Host-side launch helpers (called from eik_runtime.cu)
 // ---------------------------------------------------------------------------
@@ -555,6 +617,22 @@ cudaError_t launch_result(const T* slot, const unsigned long long* stamp, T* out
 }
 
 template <typename T>
+cudaError_t launch_slab_export(const T* slot, const unsigned long long* ups, const unsigned long long* stamp, int BX,
+                               int BY, int bz, int face, void* out, cudaStream_t s) {
+    k_slab_export<T><<<BX * BY, 64, 0, s>>>(slot, ups, stamp, BX, BY, bz, face, static_cast<FaceRec<T>*>(out));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_slab_import(T* slot, unsigned long long* ups, unsigned long long* stamp, int BX, int BY, int gbz,
+                               int obz, const void* in, int k_done, int32_t* queued, int64_t nbricks, Ctrl* C,
+                               int32_t* list_next, cudaStream_t s) {
+    k_slab_import<T><<<BX * BY, 64, 0, s>>>(slot, ups, stamp, BX, BY, gbz, obz, static_cast<const FaceRec<T>*>(in),
+                                            k_done, queued, nbricks, C, list_next);
+    return cudaGetLastError();
+}
+
+template <typename T>
 size_t loop_smem_bytes() {
     return sizeof(WarpSmem<T>) * kWarps;
 }
@@ -588,6 +666,10 @@ cudaError_t launch_restart_loop(const LoopParams<T>& P, int grid, cudaStream_t s
                                             cudaStream_t);                                                       \
     template cudaError_t launch_result<T>(const T*, const unsigned long long*, T*, int, int, int, int, int, int, \
                                           cudaStream_t);                                                         \
+    template cudaError_t launch_slab_export<T>(const T*, const unsigned long long*, const unsigned long long*, int, \
+                                               int, int, int, void*, cudaStream_t);                              \
+    template cudaError_t launch_slab_import<T>(T*, unsigned long long*, unsigned long long*, int, int, int, int,   \
+                                               const void*, int, int32_t*, int64_t, Ctrl*, int32_t*, cudaStream_t); \
     template size_t loop_smem_bytes<T>();                                                                        \
     template cudaError_t loop_occupancy<T>(int*);                                                                \
     template cudaError_t launch_restart_loop<T>(const LoopParams<T>&, int, cudaStream_t);

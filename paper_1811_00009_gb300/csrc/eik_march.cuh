@@ -497,6 +497,10 @@ struct Geo {
 template <typename T>
 __device__ __forceinline__ void enqueue_next(const LoopParams<T>& P, const Geo& G, int k, int32_t x) {
     const int s = (k + 1) % kRing;
+    if (P.pause) {                       // a sharded grid: ghost bricks belong to another GPU
+        const int bz = (x - G.boff) / (G.BX * G.BY);
+        if (bz < P.own_bz0 || bz >= P.own_bz1) return;
+    }
     if ((G.lists & 1u) && atomicMax(P.queued + s * P.nbricks + x, k + 1) < k + 1) {
         const int pos = atomicAdd(&P.ctrl->count[s], 1);
         P.list[s][pos] = x;

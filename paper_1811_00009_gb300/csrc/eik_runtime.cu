@@ -34,6 +34,12 @@ cudaError_t launch_gather_r(int, const int32_t*, const int32_t*, const T*, doubl
 template <typename T>
 cudaError_t launch_result(const T*, const unsigned long long*, T*, int, int, int, int, int, int, cudaStream_t);
 template <typename T>
+cudaError_t launch_slab_export(const T*, const unsigned long long*, const unsigned long long*, int, int, int, int, void*,
+                               cudaStream_t);
+template <typename T>
+cudaError_t launch_slab_import(T*, unsigned long long*, unsigned long long*, int, int, int, int, const void*, int,
+                               int32_t*, int64_t, Ctrl*, int32_t*, cudaStream_t);
+template <typename T>
 size_t loop_smem_bytes();
 template <typename T>
 cudaError_t loop_occupancy(int*);
@@ -98,6 +104,15 @@ struct eik_ctx {
     eik_params params{};
     eikg::Ctrl host_ctrl{};
     std::string err;
+    // part of a grid sharded in z across GPUs (eik_slab_*): the brick planes this context owns, and the
+    // restart loop's parameters between the restarts of a sharded solve
+    int own_bz0 = 0, own_bz1 = 0;
+    int zoff = 0;                  // first node plane of this part in the whole grid
+    int nz_all = 0;                // node planes of the whole grid (sources are in its coordinates)
+    bool slab = false;
+    bool slab_running = false;
+    eikg::LoopParams<float> lp_f{};
+    eikg::LoopParams<double> lp_d{};
 };
 
 namespace {
@@ -404,7 +419,7 @@ eik_status eik_add_sources(eik_ctx* c, int32_t n, const double* xyz) {
     if (c->in_flight) return fail(c, EIK_ESTATE, "eik_add_sources: a solve is in flight (call eik_wait)");
     if (n < 0) return fail(c, EIK_EINVAL, "eik_add_sources: n < 0");
     if (n > 0 && !xyz) return fail(c, EIK_EINVAL, "eik_add_sources: xyz is NULL");
-    const int dims[3] = {c->nx, c->ny, c->nz};
+    const int dims[3] = {c->nx, c->ny, c->slab ? c->nz_all : c->nz};    // (a part of a sharded grid: whole-grid z)
     const double tol = 1e-9 * c->h;
     for (int s = 0; s < n; ++s)
         for (int a = 0; a < 3; ++a) {
@@ -431,13 +446,25 @@ namespace {
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 template <typename T>
-eik_status queue_solve(eik_ctx* c, const eik_params& P) {
+eikg::LoopParams<T>& loop_params(eik_ctx* c);
+template <>
+eikg::LoopParams<float>& loop_params<float>(eik_ctx* c) { return c->lp_f; }
+template <>
+eikg::LoopParams<double>& loop_params<double>(eik_ctx* c) { return c->lp_d; }
+
+// Set up a solve (Alg. 1, work lists, control block) and, unless `slab`, queue
+// the whole restart loop.  With `slab` the context is one part of a grid
+// sharded in z: the loop's parameters are kept for eik_slab_restart, which
+// runs one restart at a time, and ghost bricks never go on a work list.
+template <typename T>
+eik_status queue_solve(eik_ctx* c, const eik_params& P, bool slab = false) {
     cudaStream_t s = c->stream;
     // ---- fixed nodes: candidates of every source, with their h/F from the device
     const eikh::Bricks geo{c->BX, c->BY, c->BZ, 0};
     std::vector<eikh::Cand> cand;
     const int nsrc = static_cast<int>(c->src.size() / 3);
-    eikh::source_candidates(c->src.data(), nsrc, c->nx, c->ny, c->nz, c->h, geo, cand);
+    eikh::source_candidates(c->src.data(), nsrc, c->nx, c->ny, c->slab ? c->nz_all : c->nz, c->h, geo, cand,
+                            c->slab ? c->zoff : 0, c->nz);
     const int nc = static_cast<int>(cand.size());
     std::vector<int32_t> cb(nc), cp(nc);
     for (int t = 0; t < nc; ++t) {
@@ -483,6 +510,14 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
     const std::vector<eikh::FixNode> uf = eikh::fixed_nodes(cand, cr, c->h);
     std::vector<int32_t> sb, enq;
     eikh::first_active(uf, geo, sb, enq);
+    if (slab) {                          // ghost bricks are marched by the GPU that owns them
+        std::vector<int32_t> own;
+        for (int32_t x : enq) {
+            const int bz = x / (c->BX * c->BY);
+            if (bz >= c->own_bz0 && bz < c->own_bz1) own.push_back(x);
+        }
+        enq.swap(own);
+    }
     const bool groups = (P.block_dim == 16) || (P.schedule != EIK_SCHED_FIXED);
     std::vector<int32_t> genq;
     if (groups) genq = eikh::groups_of(enq, geo, c->GX, c->GY, 0);
@@ -530,7 +565,7 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
     // ---- control block: restart 1 with bound_1 = 0 + stride
     eikg::Ctrl& H = c->host_ctrl;
     std::memset(&H, 0, sizeof(H));
-    H.k = enq.empty() ? 0 : 1;
+    H.k = (enq.empty() && !slab) ? 0 : 1;
     H.action = -1;
     H.pend_action = -1;
     H.bound_prev = -1.0;
@@ -540,7 +575,7 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
     H.gcount[1] = static_cast<int32_t>(genq.size());
     H.mode = (P.block_dim == 16) ? 16 : 8;
     H.r_rmin_bits = 0x7f800000u;
-    H.done = enq.empty() ? 1 : 0;
+    H.done = (enq.empty() && !slab) ? 1 : 0;
     EIK_CK(c, cudaMemcpyAsync(c->ctrl, &H, sizeof(H), cudaMemcpyHostToDevice, s));
     if (P.log_restarts) {
         const int64_t want = std::min<int64_t>(P.max_restarts, int64_t(1) << 16);
@@ -552,7 +587,7 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
             c->log_cap = want;
         }
     }
-    if (!enq.empty()) {
+    if (!enq.empty() || slab) {
         eikg::LoopParams<T> L{};
         L.nx = c->nx;
         L.ny = c->ny;
@@ -594,6 +629,16 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P) {
         L.nmax = std::max(c->nx, std::max(c->ny, c->nz));
         L.seed = static_cast<uint32_t>(P.seed);
         L.margin = static_cast<float>(P.switch_margin);
+        L.own_bz0 = 0;
+        L.own_bz1 = c->BZ;
+        if (slab) {
+            L.pause = 1;                 // one restart per launch; the host exchanges faces in between
+            L.early = 0;
+            L.own_bz0 = c->own_bz0;
+            L.own_bz1 = c->own_bz1;
+            loop_params<T>(c) = L;
+            return EIK_OK;
+        }
         if (P.loop_events[0]) EIK_CK(c, cudaEventRecord(static_cast<cudaEvent_t>(P.loop_events[0]), s));
         EIK_CK(c, eikg::launch_restart_loop<T>(L, c->loop_grid, s));
         if (P.loop_events[1]) EIK_CK(c, cudaEventRecord(static_cast<cudaEvent_t>(P.loop_events[1]), s));
@@ -748,6 +793,138 @@ eik_status eik_autotune(eik_ctx* c, int32_t rounds, double* stride_out, int32_t*
     if (block_out) *block_out = c->tuned_block;
     if (best_ms) *best_ms = median(alive[0].ms);
     return EIK_OK;
+}
+
+int64_t eik_slab_face_bytes(const eik_ctx* c) {
+    if (!c) return -1;
+    const size_t rec = (c->prec == EIK_FP32) ? sizeof(eikg::FaceRec<float>) : sizeof(eikg::FaceRec<double>);
+    return static_cast<int64_t>(rec) * c->BX * c->BY;
+}
+
+eik_status eik_slab_set(eik_ctx* c, int32_t own_bz0, int32_t own_bz1, int32_t zoff, int32_t nz_all) {
+    if (!c) return fail(nullptr, EIK_EINVAL, "eik_slab_set: ctx is NULL");
+    if (c->in_flight || c->slab_running) return fail(c, EIK_ESTATE, "eik_slab_set: a solve is in flight");
+    if (!(0 <= own_bz0 && own_bz0 < own_bz1 && own_bz1 <= c->BZ))
+        return fail(c, EIK_EINVAL, "eik_slab_set: need 0 <= own_bz0 < own_bz1 <= brick planes of the grid");
+    if (!(zoff >= 0 && zoff % 8 == 0 && zoff + c->nz <= nz_all))
+        return fail(c, EIK_EINVAL, "eik_slab_set: need zoff >= 0, a multiple of 8, and zoff + nz <= nz_all");
+    if (!c->src.empty()) return fail(c, EIK_ESTATE, "eik_slab_set: call it before adding sources");
+    c->own_bz0 = own_bz0;
+    c->own_bz1 = own_bz1;
+    c->zoff = zoff;
+    c->nz_all = nz_all;
+    c->slab = true;
+    return EIK_OK;
+}
+
+eik_status eik_slab_begin(eik_ctx* c, double stride) {
+    if (!c) return fail(nullptr, EIK_EINVAL, "eik_slab_begin: ctx is NULL");
+    if (!c->slab) return fail(c, EIK_ESTATE, "eik_slab_begin: no slab set (eik_slab_set)");
+    if (c->in_flight || c->slab_running) return fail(c, EIK_ESTATE, "eik_slab_begin: a solve is in flight");
+    // (no source is fine: a slab without one starts with an empty work list and gets work through imports)
+    if (!(stride > 0.0) || std::isinf(stride)) return fail(c, EIK_EINVAL, "eik_slab_begin: stride must be finite and > 0");
+    eik_status st = check_speed(c);
+    if (st != EIK_OK) return st;
+    eik_params P;
+    eik_params_default(&P);
+    P.stride = stride;
+    P.block_dim = 8;
+    P.width = INFINITY;
+    c->params = P;
+    st = (c->prec == EIK_FP32) ? queue_solve<float>(c, P, true) : queue_solve<double>(c, P, true);
+    if (st != EIK_OK) return st;
+    c->slab_running = true;
+    c->solved = false;
+    return EIK_OK;
+}
+
+namespace {
+// Entries of the next restart's brick list (after a restart, or after imports).
+eik_status slab_pending(eik_ctx* c, int64_t* pending) {
+    eikg::Ctrl H{};
+    EIK_CK(c, cudaStreamSynchronize(c->stream));
+    EIK_CK(c, cudaMemcpy(&H, c->ctrl, sizeof(H), cudaMemcpyDeviceToHost));
+    c->host_ctrl = H;
+    if (pending) *pending = H.count[H.k % eikg::kRing];
+    if (H.status & (eikg::kStWaitTimeout | eikg::kStRestartCap | eikg::kStRoundCap))
+        return fail(c, EIK_ETIMEOUT, "sharded solve stopped early (restart cap, round cap or a device wait limit)");
+    return EIK_OK;
+}
+}  // namespace
+
+eik_status eik_slab_restart(eik_ctx* c, int64_t* pending) {
+    if (!c) return fail(nullptr, EIK_EINVAL, "eik_slab_restart: ctx is NULL");
+    if (!c->slab_running) return fail(c, EIK_ESTATE, "eik_slab_restart: no sharded solve begun (eik_slab_begin)");
+    EIK_CK(c, cudaMemsetAsync(&c->ctrl->done, 0, sizeof(int32_t), c->stream));
+    if (c->prec == EIK_FP32) EIK_CK(c, eikg::launch_restart_loop<float>(c->lp_f, c->loop_grid, c->stream));
+    else EIK_CK(c, eikg::launch_restart_loop<double>(c->lp_d, c->loop_grid, c->stream));
+    return slab_pending(c, pending);
+}
+
+eik_status eik_slab_export(eik_ctx* c, int32_t side, void* buf) {
+    if (!c) return fail(nullptr, EIK_EINVAL, "eik_slab_export: ctx is NULL");
+    if (!c->slab_running) return fail(c, EIK_ESTATE, "eik_slab_export: no sharded solve begun");
+    if (!buf || (side != 0 && side != 1)) return fail(c, EIK_EINVAL, "eik_slab_export: side must be 0 or 1, buf not NULL");
+    const int bz = side == 0 ? c->own_bz0 : c->own_bz1 - 1, face = side == 0 ? 4 : 5;
+    if (c->prec == EIK_FP32)
+        EIK_CK(c, eikg::launch_slab_export<float>(static_cast<const float*>(c->slot), c->ups, c->stamp, c->BX, c->BY, bz,
+                                                  face, buf, c->stream));
+    else
+        EIK_CK(c, eikg::launch_slab_export<double>(static_cast<const double*>(c->slot), c->ups, c->stamp, c->BX, c->BY,
+                                                   bz, face, buf, c->stream));
+    EIK_CK(c, cudaStreamSynchronize(c->stream));
+    return EIK_OK;
+}
+
+eik_status eik_slab_import(eik_ctx* c, int32_t side, const void* buf, int64_t* pending) {
+    if (!c) return fail(nullptr, EIK_EINVAL, "eik_slab_import: ctx is NULL");
+    if (!c->slab_running) return fail(c, EIK_ESTATE, "eik_slab_import: no sharded solve begun");
+    if (!buf || (side != 0 && side != 1)) return fail(c, EIK_EINVAL, "eik_slab_import: side must be 0 or 1, buf not NULL");
+    const int gbz = side == 0 ? c->own_bz0 - 1 : c->own_bz1, obz = side == 0 ? c->own_bz0 : c->own_bz1 - 1;
+    if (gbz < 0 || gbz >= c->BZ) return fail(c, EIK_EINVAL, "eik_slab_import: no ghost plane on that side");
+    const int k_next = c->host_ctrl.k, k_done = k_next - 1;
+    const int sn = k_next % eikg::kRing;
+    int32_t* list_next = c->lists + static_cast<int64_t>(sn) * c->nbricks;
+    if (c->prec == EIK_FP32)
+        EIK_CK(c, eikg::launch_slab_import<float>(static_cast<float*>(c->slot), c->ups, c->stamp, c->BX, c->BY, gbz, obz,
+                                                  buf, k_done, c->queued, c->nbricks, c->ctrl, list_next, c->stream));
+    else
+        EIK_CK(c, eikg::launch_slab_import<double>(static_cast<double*>(c->slot), c->ups, c->stamp, c->BX, c->BY, gbz,
+                                                   obz, buf, k_done, c->queued, c->nbricks, c->ctrl, list_next,
+                                                   c->stream));
+    return slab_pending(c, pending);
+}
+
+eik_status eik_slab_end(eik_ctx* c, eik_stats* stats) {
+    if (!c) return fail(nullptr, EIK_EINVAL, "eik_slab_end: ctx is NULL");
+    if (!c->slab_running) return fail(c, EIK_ESTATE, "eik_slab_end: no sharded solve begun");
+    c->slab_running = false;
+    if (c->nfix > 0) {
+        if (c->prec == EIK_FP32)
+            EIK_CK(c, eikg::launch_restore_r<float>(c->nfix, c->d_fix_b, c->d_fix_p, static_cast<const float*>(c->d_saved_r),
+                                                    static_cast<float*>(c->rr), c->stream));
+        else
+            EIK_CK(c, eikg::launch_restore_r<double>(c->nfix, c->d_fix_b, c->d_fix_p,
+                                                     static_cast<const double*>(c->d_saved_r), static_cast<double*>(c->rr),
+                                                     c->stream));
+    }
+    eik_status st = slab_pending(c, nullptr);
+    const eikg::Ctrl& H = c->host_ctrl;
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->restarts = H.k - 1;
+        stats->marches = static_cast<int64_t>(H.marches);
+        stats->accepted = static_cast<int64_t>(H.accepted);
+        stats->solves = static_cast<int64_t>(H.solves);
+        stats->updates = static_cast<int64_t>(H.updates);
+        stats->fallbacks = static_cast<int64_t>(H.fallbacks);
+        stats->rounds = static_cast<int64_t>(H.rounds);
+        stats->final_bound = H.bound_prev;
+        stats->status = st;
+        stats->block_dim = 8;
+    }
+    if (st == EIK_OK) c->solved = true;
+    return st;
 }
 
 eik_status eik_restart_log(eik_ctx* c, eik_restart_rec* out, int64_t cap, int64_t* n) {
