@@ -33,12 +33,12 @@ if ROOT not in sys.path:
 METRIC = "Eikonal Mpoints/s at 512^3/1024^3 + HBM roofline %; learned vs fixed stride"
 ALGO_BYTES_PER_POINT = {"fp32": 8, "fp64": 16}      # read F once + write psi once
 KERNELS_PER_SOLVE = 4                                # gather_r, init_sources, restart_loop, restore_r
-# DRAM bytes and warp instructions of one k_restart_loop launch on the 1024^3 workload (fixed stride 2h, 8^3
-# blocks, FP32) from a one-pass ncu capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum =
-# 93.07 GB + 53.32 GB; smsp__inst_executed.sum = 168.03 G), per node; profiles/launches_c4_1024_fixed2h.md
-# gives the commands.
-NCU_TRAFFIC_PER_NODE = {"fp32": (93.07e9 + 53.32e9) / 1024 ** 3}
-NCU_INST_PER_NODE = {"fp32": 168.03e9 / 1024 ** 3}
+# DRAM bytes and warp instructions per node of k_restart_loop (fixed stride 2h, 8^3 blocks, FP32) from an ncu
+# capture of the same workload family at 512^3 (dram__bytes_read.sum + dram__bytes_write.sum = 9.387 GB +
+# 4.636 GB; smsp__inst_executed.sum = 23.517 G over 512^3 nodes), scaled to the launch by its node count;
+# profiles/k_restart_loop_c4_512_fixed2h.md gives the command.
+NCU_TRAFFIC_PER_NODE = {"fp32": (9.387e9 + 4.636e9) / 512 ** 3}
+NCU_INST_PER_NODE = {"fp32": 23.517e9 / 512 ** 3}
 ISSUE_PER_SM_CYCLE = 4          # warp schedulers per SM, one warp instruction per cycle each
 
 
@@ -404,7 +404,7 @@ def run_ours(args):
     traffic_b = traffic * w.npoints if traffic else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic_b,
-            "traffic_source": ("ncu one-pass DRAM capture of a full 1024^3 launch (fixed 2h), per node x nodes"
+            "traffic_source": ("ncu DRAM capture of the 512^3 launch of the same family (fixed 2h), per node x nodes"
                                if traffic else None),
             "dram_gbs": traffic_b / (loop_avg_ms * 1e-3) / 1e9 if traffic_b else None,
             "dram_frac": traffic_b / (loop_avg_ms * 1e-3) / 1e9 / peak if traffic_b else None,
@@ -529,7 +529,8 @@ def run_ours(args):
         pk = sms * ISSUE_PER_SM_CYCLE * mhz * 1e6
         roof["issue"] = {"achieved": ach, "peak": pk, "unit": "warp instructions/s", "frac": ach / pk,
                          "inst_per_node": inst, "sms": sms, "sm_mhz": mhz,
-                         "source": "ncu smsp__inst_executed.sum, one-pass capture of a full 1024^3 launch (fixed 2h)"}
+                         "source": "ncu smsp__inst_executed.sum of the 512^3 launch of the same family (fixed 2h), "
+                                   "per node x nodes"}
     s0 = stats[-1]
     line = {"metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
