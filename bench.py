@@ -515,6 +515,32 @@ def run_ours(args):
         del F64
         fp64 = {"mpoints_per_s": w.npoints / (ms64 * 1e-3) / 1e6, "loop_ms": ms64, "restarts": st64["restarts"],
                 "config": "FP64 storage and arithmetic, fixed stride 2h, 8^3 blocks, same workload"}
+    # 32^3 blocks (one CTA of 1024 threads per block, FP32, fixed stride) on the same workload, beside the
+    # 8^3 solve: one warm-up, one timed solve, and the result against the 8^3 solve's bit for bit
+    b32 = None
+    if not args.no_block32 and prec == "fp32" and rank == 0:
+        c32 = eik.eik_create(w.dims, w.h, Fd, "fp32")
+        eik.eik_add_sources(c32, w.sources)
+        eik.eik_solve_ex(c32, 1.5 * w.h, block_dim=8)
+        o8 = torch.empty_like(Fd)
+        eik.eik_result(c32, o8)
+        kw32 = dict(block_dim=32, window=4.0)
+        eik.eik_solve_ex(c32, 4.0 * w.h, **kw32)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e1.record(stream)
+        st32 = eik.eik_solve_ex(c32, 4.0 * w.h, loop_events=(e0, e1), **kw32)
+        torch.cuda.synchronize()
+        ms32 = e0.elapsed_time(e1)
+        o32 = torch.empty_like(Fd)
+        eik.eik_result(c32, o32)
+        same = bool(torch.equal(o8, o32))
+        eik.eik_destroy(c32)
+        del o8, o32
+        b32 = {"mpoints_per_s": w.npoints / (ms32 * 1e-3) / 1e6, "loop_ms": ms32, "restarts": st32["restarts"],
+               "accepted_per_node": st32["accepted"] / w.npoints, "solves_per_node": st32["solves"] / w.npoints,
+               "bitwise_equal_to_8": same,
+               "config": "32^3 blocks, one CTA of 1024 threads each, fixed stride 4h, window 4, same workload"}
     batch = None
     if not args.no_batch and rank == 0:
         batch = batch_bench(eik, synth, args.batch_steps, 3, args.tune_rounds, dev)
@@ -548,7 +574,7 @@ def run_ours(args):
             "solve": {"restarts": s0["restarts"], "marches": s0["marches"], "accepted": s0["accepted"],
                       "solves": s0["solves"], "updates": s0["updates"], "fallbacks": s0["fallbacks"],
                       "rounds": s0["rounds"], "loop_ms": loop_avg_ms},
-            "error_vs_oracle": err, "fp64_solve": fp64, "batch": batch}
+            "error_vs_oracle": err, "fp64_solve": fp64, "block32_solve": b32, "batch": batch}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -571,6 +597,7 @@ def main():
     ap.add_argument("--no-cpu-block", action="store_true",
                     help="skip the multi-core CPU block solver on the full workload (and the full-size error)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 solve of the same workload")
+    ap.add_argument("--no-block32", action="store_true", help="skip the 32^3-block solve of the same workload")
     ap.add_argument("--ref-n", type=int, default=128)
     ap.add_argument("--e2e-steps", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -130,9 +130,13 @@ typedef struct {
     double stride;          /* bound increment in psi units (> 0; +inf = the naive block method); 0 selects
                                the learned schedule (as schedule = EIK_SCHED_LEARNED, with 2h for restarts
                                1-2) */
-    int32_t block_dim;      /* block edge in nodes: 8 (one warp per block) or 16 (one CTA per block of
-                               2x2x2 bricks); 0 = picked: by the network under the learned schedule (8 for
-                               restarts 1-2), else the edge eik_autotune chose for the context, else 8 */
+    int32_t block_dim;      /* block edge in nodes: 8 (one warp per block), 16 (one CTA per block of
+                               2x2x2 bricks) or 32 (one CTA of 1024 threads per 32^3 block, its tile in
+                               shared memory; FP32 and the fixed schedule only, no restart log: else
+                               EIK_ENOTSUP; the context allocates the 32^3 layout on its first such solve:
+                               two copies of psi and h/F, about 3.1x the grid's FP32 bytes); 0 = picked: by the
+                               network under the learned schedule (8 for restarts 1-2), else the edge
+                               eik_autotune chose for the context, else 8 */
     int32_t schedule;       /* eik_schedule */
     double window;          /* acceptance window factor omega: each march round accepts every band
                                point within omega * h / F_max(block) of the band minimum
@@ -156,7 +160,8 @@ typedef struct {
 /* Per-solve statistics, filled by eik_solve / eik_wait. */
 typedef struct {
     int64_t restarts;       /* nr: iterations of the restart loop of Alg. 6 */
-    int64_t marches;        /* block marches (active or flagged blocks, summed over restarts) */
+    int64_t marches;        /* block marches (active or flagged blocks, summed over restarts), in 8^3
+                               bricks: a 16^3 block counts 8, a 32^3 block 64 */
     int64_t accepted;       /* band points accepted (heap pops in Alg. 4), refreshes included */
     int64_t solves;         /* upwind solves (Alg. 3 calls) */
     int64_t updates;        /* solves that lowered psi (Alg. 2 accepted updates) */
@@ -199,8 +204,9 @@ void eik_params_default(eik_params *p);
  *              restart from restart 3 on; restarts 1-2 take 2h.  The
  *              context's network weights are used (every context starts
  *              with the shipped ones; eik_set_schedule replaces them).
- *   block_dim  8 or 16; 0 = picked (the network under the learned schedule,
- *              else the edge eik_autotune chose for the context, else 8).
+ *   block_dim  8, 16 or 32 (see eik_params.block_dim); 0 = picked (the
+ *              network under the learned schedule, else the edge
+ *              eik_autotune chose for the context, else 8).
  *   stats      nullable.
  * The result does not depend on the stride, the schedule or the block edge,
  * bit for bit (the root of Alg. 3 is evaluated as a monotone function of the

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libeik.so")
-SOURCES = ["eik_kernels.cu", "eik_runtime.cu", "eik_batch.cu", "eik_noalloc.cu", "eik_mlp.cu"]
+SOURCES = ["eik_kernels.cu", "eik_runtime.cu", "eik_batch.cu", "eik_noalloc.cu", "eik_mlp.cu", "eik_block32.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-O2,-ffp-contract=off",
          "--expt-relaxed-constexpr",

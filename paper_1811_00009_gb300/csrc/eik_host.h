@@ -155,9 +155,9 @@ inline void first_active(const std::vector<FixNode>& fix, const Bricks& g, std::
 inline const char* param_error(const eik_params& p, eik_status* code) {
     *code = EIK_EINVAL;
     if (!(p.stride > 0.0)) return "stride must be > 0 (+inf allowed), or 0 for the learned schedule";
-    if (p.block_dim != 0 && p.block_dim != 8 && p.block_dim != 16) {
+    if (p.block_dim != 0 && p.block_dim != 8 && p.block_dim != 16 && p.block_dim != 32) {
         *code = EIK_ENOTSUP;
-        return "block_dim must be 8 or 16 (or 0)";
+        return "block_dim must be 8, 16 or 32 (or 0)";
     }
     if (p.schedule != EIK_SCHED_FIXED && p.schedule != EIK_SCHED_LEARNED && p.schedule != EIK_SCHED_RANDOM)
         return "schedule must be EIK_SCHED_FIXED, EIK_SCHED_LEARNED or EIK_SCHED_RANDOM";

@@ -39,6 +39,16 @@ cudaError_t launch_slab_export(const T*, const unsigned long long*, const unsign
 template <typename T>
 cudaError_t launch_slab_import(T*, unsigned long long*, unsigned long long*, int, int, int, int, const void*, int,
                                int32_t*, int64_t, Ctrl*, int32_t*, cudaStream_t);
+size_t block32_smem_bytes();
+int block32_edge_values();
+cudaError_t block32_occupancy(int* per_sm);
+cudaError_t block32_layout(const float*, int, int, int, float*, int, int, int64_t, cudaStream_t);
+cudaError_t block32_init(int, const int32_t*, const int32_t*, const double*, int, const int32_t*, int, const int32_t*,
+                         float*, unsigned*, unsigned long long*, int32_t*, float*, float*, int32_t*, cudaStream_t);
+cudaError_t block32_restore(int, const int32_t*, const int32_t*, const float*, float*, cudaStream_t);
+cudaError_t block32_result(const float*, const unsigned long long*, float*, int, int, int, int, int, cudaStream_t);
+cudaError_t block32_loop(int, int, int, int64_t, float*, unsigned*, unsigned long long*, const float*, int32_t*,
+                         int32_t*, Ctrl*, float, float, double, int64_t, long long, int, cudaStream_t);
 template <typename T>
 size_t loop_smem_bytes();
 template <typename T>
@@ -113,6 +123,20 @@ struct eik_ctx {
     bool slab_running = false;
     eikg::LoopParams<float> lp_f{};
     eikg::LoopParams<double> lp_d{};
+    // 32^3 blocks (block_dim 32, FP32): their own layout, allocated on the first such solve
+    struct {
+        int NBX = 0, NBY = 0, NBZ = 0;
+        int64_t nblk = 0;
+        float* rr = nullptr;               // h/F in 32^3 blocks (from the brick layout)
+        float* copy = nullptr;
+        unsigned* ups = nullptr;
+        unsigned long long* stamp = nullptr;
+        int32_t* queued = nullptr;
+        int32_t* lists = nullptr;
+        bool rr_valid = false;
+        int grid = 0;
+    } b32;
+    int last_edge = 8;                 // block edge of the last solve (where eik_result finds psi)
 };
 
 namespace {
@@ -142,6 +166,9 @@ void free_all(eik_ctx* c) {
     void* ptrs[] = {c->rr,    c->slot,  c->ups,   c->stamp,   c->queued, c->lists, c->done, c->qgroup, c->glists,
                     c->ctrl,  c->log, c->scratch, c->fstage, c->d_mlp};
     for (void* p : ptrs)
+        if (p) cudaFree(p);
+    void* p32[] = {c->b32.rr, c->b32.copy, c->b32.ups, c->b32.stamp, c->b32.queued, c->b32.lists};
+    for (void* p : p32)
         if (p) cudaFree(p);
     if (c->h_err) cudaFreeHost(c->h_err);
     if (c->h_gather) cudaFreeHost(c->h_gather);
@@ -174,6 +201,7 @@ eik_status upload_speed(eik_ctx* c, const void* F, int F_on_device, bool wait = 
         Fd = c->fstage;
     }
     const int seq = ++c->upload_seq;
+    c->b32.rr_valid = false;
     if (c->prec == EIK_FP32)
         EIK_CK(c, eikg::launch_layout_speed<float>(static_cast<const float*>(Fd), static_cast<float*>(c->rr), c->nx,
                                                    c->ny, c->nz, c->BX, c->BY, c->nbricks, c->h, c->d_err, seq,
@@ -204,6 +232,9 @@ eik_status check_speed(eik_ctx* c) {
 
 // psi of the last solve in grid order -> dst (device memory), queued on the stream.
 cudaError_t queue_result(eik_ctx* c, void* dst) {
+    if (c->last_edge == 32)
+        return eikg::block32_result(c->b32.copy, c->b32.stamp, static_cast<float*>(dst), c->nx, c->ny, c->nz, c->b32.NBX,
+                                    c->b32.NBY, c->stream);
     if (c->prec == EIK_FP32)
         return eikg::launch_result<float>(static_cast<const float*>(c->slot), c->stamp, static_cast<float*>(dst),
                                           c->nx, c->ny, 0, c->nz, c->BX, c->BY, c->stream);
@@ -649,6 +680,168 @@ eik_status queue_solve(eik_ctx* c, const eik_params& P, bool slab = false) {
     return EIK_OK;
 }
 
+// The solve with 32^3 blocks (FP32, fixed stride): its layout is allocated and
+// h/F re-laid from the bricks on first use; Alg. 1 as in queue_solve, in the
+// blocks' coordinates.
+eik_status queue_solve32(eik_ctx* c, const eik_params& P) {
+    cudaStream_t s = c->stream;
+    auto& B = c->b32;
+    if (!B.copy) {
+        B.NBX = (c->nx + 31) / 32;
+        B.NBY = (c->ny + 31) / 32;
+        B.NBZ = (c->nz + 31) / 32;
+        B.nblk = int64_t(B.NBX) * B.NBY * B.NBZ;
+        const size_t nb = static_cast<size_t>(B.nblk);
+        struct {
+            void** p;
+            size_t bytes;
+        } allocs[] = {
+            {reinterpret_cast<void**>(&B.rr), nb * 32768 * sizeof(float)},
+            {reinterpret_cast<void**>(&B.copy), nb * 2 * static_cast<size_t>(eikg::block32_edge_values()) * sizeof(float)},
+            {reinterpret_cast<void**>(&B.ups), nb * 2 * 6 * 32 * sizeof(unsigned)},
+            {reinterpret_cast<void**>(&B.stamp), nb * sizeof(unsigned long long)},
+            {reinterpret_cast<void**>(&B.queued), eikg::kRing * nb * sizeof(int32_t)},
+            {reinterpret_cast<void**>(&B.lists), eikg::kRing * nb * sizeof(int32_t)},
+        };
+        for (auto& a : allocs) {
+            const cudaError_t e = dalloc(a.p, a.bytes);
+            if (e != cudaSuccess) return fail(c, EIK_ENOMEM, std::string("32^3 blocks: cudaMalloc failed: ") + cudaGetErrorString(e));
+        }
+        int per_sm = 0;
+        EIK_CK(c, eikg::block32_occupancy(&per_sm));
+        if (per_sm < 1) return fail(c, EIK_ENOTSUP, "32^3 blocks: one CTA of 1024 threads does not fit an SM");
+        B.grid = per_sm * c->sms;
+    }
+    if (!B.rr_valid) {
+        EIK_CK(c, eikg::block32_layout(static_cast<const float*>(c->rr), c->BX, c->BY, c->BZ, B.rr, B.NBX, B.NBY, B.nblk, s));
+        B.rr_valid = true;
+    }
+    // ---- fixed nodes (Alg. 1): candidates and their h/F from the brick layout, then block coordinates
+    const eikh::Bricks geo{c->BX, c->BY, c->BZ, 0};
+    std::vector<eikh::Cand> cand;
+    const int nsrc = static_cast<int>(c->src.size() / 3);
+    eikh::source_candidates(c->src.data(), nsrc, c->nx, c->ny, c->nz, c->h, geo, cand);
+    const int nc = static_cast<int>(cand.size());
+    std::vector<int32_t> cb(nc), cp(nc);
+    for (int t = 0; t < nc; ++t) {
+        cb[t] = cand[t].b;
+        cp[t] = cand[t].p;
+    }
+    const size_t need = align_up(nc * 4) * 2 + align_up(static_cast<size_t>(nc) * 8) * 2 + align_up(nc * 4) * 4 +
+                        align_up(nc * 7 * 4) + 4096;
+    if (need > c->scratch_cap) {
+        if (c->scratch) cudaFree(c->scratch);
+        c->scratch = nullptr;
+        c->scratch_cap = 0;
+        EIK_CK(c, cudaMalloc(&c->scratch, need));
+        c->scratch_cap = need;
+    }
+    char* sp = static_cast<char*>(c->scratch);
+    auto carve = [&](size_t bytes) {
+        char* r = sp;
+        sp += align_up(bytes);
+        return r;
+    };
+    int32_t* d_cb = reinterpret_cast<int32_t*>(carve(nc * 4));
+    int32_t* d_cp = reinterpret_cast<int32_t*>(carve(nc * 4));
+    std::vector<double> cr(nc);
+    if (nc > 0) {
+        if (nc > c->gather_cap) {
+            if (c->h_gather) cudaFreeHost(c->h_gather);
+            c->h_gather = nullptr;
+            c->gather_cap = 0;
+            EIK_CK(c, cudaHostAlloc(reinterpret_cast<void**>(&c->h_gather), static_cast<size_t>(nc) * 8,
+                                    cudaHostAllocMapped));
+            EIK_CK(c, cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->d_gather), c->h_gather, 0));
+            c->gather_cap = nc;
+        }
+        EIK_CK(c, cudaMemcpyAsync(d_cb, cb.data(), nc * 4, cudaMemcpyHostToDevice, s));
+        EIK_CK(c, cudaMemcpyAsync(d_cp, cp.data(), nc * 4, cudaMemcpyHostToDevice, s));
+        EIK_CK(c, eikg::launch_gather_r<float>(nc, d_cb, d_cp, static_cast<const float*>(c->rr), c->d_gather, s));
+        EIK_CK(c, cudaStreamSynchronize(s));
+        for (int t = 0; t < nc; ++t) cr[t] = reinterpret_cast<volatile double*>(c->h_gather)[t];
+    }
+    const std::vector<eikh::FixNode> uf = eikh::fixed_nodes(cand, cr, c->h);
+    struct Fix32 {
+        int32_t b, p;
+        double v;
+    };
+    std::vector<Fix32> f32;
+    std::vector<int32_t> sb, enq;
+    for (const auto& f : uf) {
+        const int bx8 = f.b % c->BX, by8 = (f.b / c->BX) % c->BY, bz8 = f.b / (c->BX * c->BY);
+        const int i = bx8 * 8 + (f.p & 7), j = by8 * 8 + ((f.p >> 3) & 7), k = bz8 * 8 + (f.p >> 6);
+        const int bx = i >> 5, by = j >> 5, bz = k >> 5, x = i & 31, y = j & 31, z = k & 31;
+        const int32_t b = (bz * B.NBY + by) * B.NBX + bx;
+        f32.push_back({b, (z * 32 + y) * 32 + x, f.v});
+        sb.push_back(b);
+        enq.push_back(b);
+        // neighbours whose ghost layer holds the fixed node (Alg. 1 over Xi^ib)
+        if (x == 0 && bx > 0) enq.push_back(b - 1);
+        if (x == 31 && bx < B.NBX - 1) enq.push_back(b + 1);
+        if (y == 0 && by > 0) enq.push_back(b - B.NBX);
+        if (y == 31 && by < B.NBY - 1) enq.push_back(b + B.NBX);
+        if (z == 0 && bz > 0) enq.push_back(b - B.NBX * B.NBY);
+        if (z == 31 && bz < B.NBZ - 1) enq.push_back(b + B.NBX * B.NBY);
+    }
+    std::sort(sb.begin(), sb.end());
+    sb.erase(std::unique(sb.begin(), sb.end()), sb.end());
+    std::sort(enq.begin(), enq.end());
+    enq.erase(std::unique(enq.begin(), enq.end()), enq.end());
+    const int nfix = static_cast<int>(f32.size());
+    std::vector<int32_t> fb(nfix), fp(nfix);
+    std::vector<double> fv(nfix);
+    for (int t = 0; t < nfix; ++t) {
+        fb[t] = f32[t].b;
+        fp[t] = f32[t].p;
+        fv[t] = f32[t].v;
+    }
+    c->d_fix_b = reinterpret_cast<int32_t*>(carve(nfix * 4));
+    c->d_fix_p = reinterpret_cast<int32_t*>(carve(nfix * 4));
+    double* d_fv = reinterpret_cast<double*>(carve(static_cast<size_t>(nfix) * 8));
+    int32_t* d_sb = reinterpret_cast<int32_t*>(carve(sb.size() * 4));
+    int32_t* d_enq = reinterpret_cast<int32_t*>(carve(enq.size() * 4));
+    c->d_saved_r = carve(nfix * sizeof(float));
+    c->nfix = nfix;
+    if (nfix > 0) {
+        EIK_CK(c, cudaMemcpyAsync(c->d_fix_b, fb.data(), nfix * 4, cudaMemcpyHostToDevice, s));
+        EIK_CK(c, cudaMemcpyAsync(c->d_fix_p, fp.data(), nfix * 4, cudaMemcpyHostToDevice, s));
+        EIK_CK(c, cudaMemcpyAsync(d_fv, fv.data(), nfix * 8, cudaMemcpyHostToDevice, s));
+        EIK_CK(c, cudaMemcpyAsync(d_sb, sb.data(), sb.size() * 4, cudaMemcpyHostToDevice, s));
+        EIK_CK(c, cudaMemcpyAsync(d_enq, enq.data(), enq.size() * 4, cudaMemcpyHostToDevice, s));
+    }
+    const size_t nb = static_cast<size_t>(B.nblk);
+    EIK_CK(c, cudaMemsetAsync(B.stamp, 0xFF, nb * sizeof(unsigned long long), s));
+    EIK_CK(c, cudaMemsetAsync(B.queued, 0xFF, eikg::kRing * nb * sizeof(int32_t), s));
+    if (nfix > 0)
+        EIK_CK(c, eikg::block32_init(nfix, c->d_fix_b, c->d_fix_p, d_fv, static_cast<int>(sb.size()), d_sb,
+                                     static_cast<int>(enq.size()), d_enq, B.copy, B.ups, B.stamp, B.queued + nb, B.rr,
+                                     static_cast<float*>(c->d_saved_r), B.lists + nb, s));
+    eikg::Ctrl& H = c->host_ctrl;
+    std::memset(&H, 0, sizeof(H));
+    H.k = enq.empty() ? 0 : 1;
+    H.action = -1;
+    H.pend_action = -1;
+    H.bound_prev = -1.0;
+    H.stride = P.stride;
+    H.bound = std::fmin(P.stride, P.width);
+    H.count[1] = static_cast<int32_t>(enq.size());
+    H.mode = 32;
+    H.r_rmin_bits = 0x7f800000u;
+    H.done = enq.empty() ? 1 : 0;
+    EIK_CK(c, cudaMemcpyAsync(c->ctrl, &H, sizeof(H), cudaMemcpyHostToDevice, s));
+    if (!enq.empty()) {
+        if (P.loop_events[0]) EIK_CK(c, cudaEventRecord(static_cast<cudaEvent_t>(P.loop_events[0]), s));
+        EIK_CK(c, eikg::block32_loop(B.NBX, B.NBY, B.NBZ, B.nblk, B.copy, B.ups, B.stamp, B.rr, B.queued, B.lists, c->ctrl,
+                                     static_cast<float>(P.window), static_cast<float>(P.fallback_tau), P.width,
+                                     P.max_restarts, P.wait_polls > 0 ? P.wait_polls : eikg::kWaitPolls, B.grid, s));
+        if (P.loop_events[1]) EIK_CK(c, cudaEventRecord(static_cast<cudaEvent_t>(P.loop_events[1]), s));
+    }
+    if (nfix > 0)
+        EIK_CK(c, eikg::block32_restore(nfix, c->d_fix_b, c->d_fix_p, static_cast<const float*>(c->d_saved_r), B.rr, s));
+    return EIK_OK;
+}
+
 eik_status check_params(eik_ctx* c, const eik_params* p) {
     if (!p) return fail(c, EIK_EINVAL, "params is NULL");
     eik_status code;
@@ -684,7 +877,16 @@ eik_status eik_solve_async(eik_ctx* c, const eik_params* params) {
     if (P.window == 0.0) P.window = 2.0;
     if (P.width == 0.0) P.width = INFINITY;
     c->params = P;
-    st = (c->prec == EIK_FP32) ? queue_solve<float>(c, P) : queue_solve<double>(c, P);
+    if (P.block_dim == 32) {
+        if (c->prec != EIK_FP32) return fail(c, EIK_ENOTSUP, "32^3 blocks are single precision only");
+        if (P.schedule != EIK_SCHED_FIXED) return fail(c, EIK_ENOTSUP, "32^3 blocks take a fixed stride");
+        if (P.log_restarts) return fail(c, EIK_ENOTSUP, "32^3 blocks keep no restart log");
+        st = queue_solve32(c, P);
+        c->last_edge = 32;
+    } else {
+        st = (c->prec == EIK_FP32) ? queue_solve<float>(c, P) : queue_solve<double>(c, P);
+        c->last_edge = 8;
+    }
     if (st != EIK_OK) return st;
     c->in_flight = true;
     c->solved = false;
@@ -831,6 +1033,7 @@ eik_status eik_slab_begin(eik_ctx* c, double stride) {
     P.block_dim = 8;
     P.width = INFINITY;
     c->params = P;
+    c->last_edge = 8;
     st = (c->prec == EIK_FP32) ? queue_solve<float>(c, P, true) : queue_solve<double>(c, P, true);
     if (st != EIK_OK) return st;
     c->slab_running = true;
