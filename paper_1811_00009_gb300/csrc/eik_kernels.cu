@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P
         // restart k (fixed stride and 8^3 blocks only; the next bound is then
         // known).  One march call site for both.
         for (;;) {
-            int32_t b = -1;
+            int32_t b = -1, pf = -1;
             int kk = k;
             if (!L.waiting) {
                 int i = -1;
@@ -331,7 +331,13 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P
                     L.claim = -1;
                 }
                 i = __shfl_sync(kFull, i, 0);
-                if (i >= 0) b = take_entry(P.list[s], i, false, 0, lane);
+                if (i >= 0) {
+                    b = take_entry(P.list[s], i, false, 0, lane);
+                    // the entry one launch-width further down, for the march to prefetch
+                    const int i2 = i + static_cast<int>(gridDim.x) * kWarps;
+                    if (i2 < L.n) pf = __ldcg(P.list[s] + i2);
+                    if (pf >= P.nbricks) pf = -1;
+                }
                 if (b < 0) {
                     if (any) flush_acc(C, acc, lane);
                     any = false;
@@ -389,7 +395,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_restart_loop(LoopParams<T> P
                             ahead ? pick<T>(L.bound, L.bound_f) : pick<T>(L.bprev, L.bprev_f),
                             ahead ? pick<T>(L.next_bound, L.next_f) : pick<T>(L.bound, L.bound_f),
                             (ahead ? L.grow_next : L.grow) != 0, pick<T>(P.window, P.window_f), lane, acc,
-                            L.early != 0 || ahead);
+                            L.early != 0 || ahead, pf);
             any = true;
         }
         if (__ldcg(&C->done)) return;

@@ -361,6 +361,12 @@ struct __align__(16) WarpSmem {
     uint32_t fxob[16];      // bit per brick node: fixed, barrier or padding node (never solved)
 };
 
+// Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) of global memory
+// into L2, without a destination or a completion to wait for.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ int halo_of(int p) {
     const int x = p & 7, y = (p >> 3) & 7, z = p >> 6;
     return ((z + 1) * 10 + (y + 1)) * 10 + (x + 1);
@@ -530,7 +536,8 @@ __device__ __forceinline__ void enqueue_next(const LoopParams<T>& P, const Geo& 
 // one block of the paper.
 template <typename T, bool GROUP>
 __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int warp, int32_t b, unsigned gmask,
-                      int k, T bprev, T bound, bool grow, T window, int lane, MarchAcc& acc, bool publish) {
+                      int k, T bprev, T bound, bool grow, T window, int lane, MarchAcc& acc, bool publish,
+                      int32_t pf = -1) {
     __shared__ T s_wmin[kWarps];
     __shared__ T s_bmin[2][kWarps];            // group rounds: band minima, by round parity
     WarpSmem<T>& S = SW[warp];
@@ -564,6 +571,9 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
         unsigned long long wst[6];
 #pragma unroll
         for (int f = 0; f < 6; ++f) wst[f] = nbr[f] >= 0 ? __ldcg(P.stamp + nbr[f]) : kUntouched;
+        // a brick further down this restart's list (pf >= 0): its stamp now, and
+        // once it has landed (below) bulk L2 prefetches of its h/F and latest copy
+        const unsigned long long pst = (pf >= 0 && lane == 0) ? __ldcg(P.stamp + pf) : kUntouched;
         // fixed nodes (r < 0) and barrier/padding nodes (r = +inf) are never solved
         FXOB = 0;
         {
@@ -620,6 +630,11 @@ __device__ void march(const LoopParams<T>& P, const Geo& G, WarpSmem<T>* SW, int
                 else off = u;
                 load2_cg(src + off, fv0[f], fv1[f]);
             }
+        }
+        if (pf >= 0 && lane == 0) {
+            prefetch_l2(P.rr + static_cast<int64_t>(pf) * kBrick, kBrick * sizeof(T));
+            if (pst != kUntouched)
+                prefetch_l2(P.slot + (static_cast<int64_t>(pf) * 2 + stamp_copy(pst)) * kSlot, kSlot * sizeof(T));
         }
         // ---- the band at the start of the march (marked as the values land in
         // shared memory): the brick's finite nodes above the previous bound, and
