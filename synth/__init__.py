@@ -26,7 +26,7 @@ import numpy as np
 __all__ = [
     "splitmix64", "uniform", "normal", "grid_h", "node_coords",
     "speed_const", "speed_sines", "speed_layers", "speed_grf", "grf_modes",
-    "speed_paper_case", "round_to", "Workload", "workload", "batch_workloads",
+    "speed_paper_case", "speed_paper_case_slab", "round_to", "Workload", "workload", "batch_workloads",
     "random_sources",
 ]
 
@@ -160,18 +160,27 @@ def speed_paper_case(case: int, n: int) -> Tuple[np.ndarray, float, np.ndarray]:
     expressed in this module's node convention (origin at grid point 0).
     """
     h = 1.0 / n
+    F = speed_paper_case_slab(case, n, 0, n)
+    src = np.array([[0.5 - 0.5 * h] * 3])    # the centre, measured from grid point 0
+    return F, h, src
+
+
+def speed_paper_case_slab(case: int, n: int, z0: int, z1: int) -> np.ndarray:
+    """Planes z0 <= k < z1 of speed_paper_case(case, n)'s F (same values), shape (z1 - z0, n, n)."""
+    h = 1.0 / n
     c = -0.5 + (np.arange(n) + 0.5) * h
     X = c[None, None, :]
     Y = c[None, :, None]
-    Z = c[:, None, None]
+    Z = c[z0:z1, None, None]
+    m = z1 - z0
     if case == 1:
-        F = np.ones((n, n, n))
+        F = np.ones((m, n, n))
     elif case == 2:
         F = 1.0 + 0.5 * np.sin(20 * math.pi * X) * np.sin(20 * math.pi * Y) * np.sin(20 * math.pi * Z)
     elif case == 3:
         F = 1.0 - 0.99 * np.sin(2 * math.pi * X) * np.sin(2 * math.pi * Y) * np.sin(2 * math.pi * Z)
     elif case == 4:
-        F = np.ones((n, n, n))
+        F = np.ones((m, n, n))
         R = np.sqrt(X * X + Y * Y + Z * Z)
         r = np.sqrt(X * X + Y * Y) + 0.0 * Z
         w = 1.0 / 24.0
@@ -182,9 +191,7 @@ def speed_paper_case(case: int, n: int) -> Tuple[np.ndarray, float, np.ndarray]:
             F[shell & ~hole] = 0.0
     else:
         raise ValueError("case must be 1..4")
-    F = np.ascontiguousarray(np.broadcast_to(F, (n, n, n)))
-    src = np.array([[0.5 - 0.5 * h] * 3])    # the centre, measured from grid point 0
-    return F, h, src
+    return np.ascontiguousarray(np.broadcast_to(F, (m, n, n)))
 
 
 def round_to(F: np.ndarray, precision: str) -> np.ndarray:
