@@ -2,9 +2,9 @@
 
 One step = one full solve of the block-based restarted narrow-band method
 (initialisation, every restart's march and exchange, activation) on the 1024^3
-workload: node grid h = 1/1023, F = exp(g) with g a smooth random field (std
-0.5, correlation length 0.05), point source at the centre, FP32 storage with
-the FP64 root fallback.  Inputs are resident in HBM when the timed region
+workload: node grid h = 1/1023, F = exp(g) with g a Gaussian random field (white
+noise smoothed on the grid by a Gaussian; std 0.5, correlation length 0.05),
+point source at the centre, FP32 storage with the FP64 root fallback.  Inputs are resident in HBM when the timed region
 starts; they are larger than L2, so no flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -562,7 +562,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
             "data": "synthetic",
-            "config": {"workload": (f"C4: {n}^3 node grid, h=1/{n - 1}, F=exp(g) random field std 0.5 corr 0.05, "
+            "config": {"workload": (f"C4: {n}^3 node grid, h=1/{n - 1}, F=exp(g), g white noise smoothed by a Gaussian, std 0.5 corr 0.05, "
                                     f"centre source, {prec.upper()} (FP64 root fallback), "
                                     + ("learned stride/block schedule" if args.schedule == "learned" else
                                        f"fixed stride {args.stride_h:g}h, 8^3 blocks")),

@@ -25,7 +25,7 @@ import numpy as np
 
 __all__ = [
     "splitmix64", "uniform", "normal", "grid_h", "node_coords",
-    "speed_const", "speed_sines", "speed_layers", "speed_grf", "grf_modes",
+    "speed_const", "speed_sines", "speed_layers", "speed_grf", "grf_field", "speed_grf_torch",
     "speed_paper_case", "speed_paper_case_slab", "round_to", "Workload", "workload", "batch_workloads",
     "random_sources",
 ]
@@ -96,59 +96,99 @@ def speed_layers(dims: Sequence[int], seed: int, nlayers: int = 16,
     return np.broadcast_to(vals[layer][:, None, None], (nz, ny, nx)).copy()
 
 
-def grf_modes(seed: int, ell: float = 0.05, modes: int = 64) -> Tuple[np.ndarray, np.ndarray]:
-    """Wave vectors (modes, 3) and phases (modes,) of a random-Fourier-mode field.
-
-    A sum of M cosines with wave vectors drawn from N(0, I/ell^2) and uniform
-    phases has covariance exp(-|r|^2 / (2 ell^2)) in the limit of many modes
-    (Bochner's theorem; spectral synthesis of a stationary Gaussian field).
-    """
-    k = normal(seed, 5, 3 * modes).reshape(modes, 3) / ell
-    phi = 2.0 * math.pi * uniform(seed, 6, modes)
-    return k, phi
+def _gauss_multiplier(n: int, h: float, s: float, real: bool = False) -> np.ndarray:
+    """Fourier multiplier of a periodic smoothing by a Gaussian of std s (physical units) along an axis of
+    n nodes with spacing h: exp(-2 pi^2 s^2 f^2) at the FFT frequencies f (rfft frequencies if real)."""
+    f = np.fft.rfftfreq(n, d=h) if real else np.fft.fftfreq(n, d=h)
+    return np.exp(-2.0 * (math.pi * s * f) ** 2)
 
 
-def speed_grf(dims: Sequence[int], h: float, seed: int, std: float = 0.5,
-              ell: float = 0.05, modes: int = 64) -> np.ndarray:
-    """F = exp(g), g a smooth stationary random field with std `std`, correlation length `ell`."""
+def grf_field(dims: Sequence[int], h: float, seed: int, std: float = 0.5, ell: float = 0.05) -> np.ndarray:
+    """g: white N(0, 1) noise from this module's generator on the node grid (stream 5), convolved
+    periodically with a separable Gaussian of std ell/sqrt(2) per axis -- so that its covariance is
+    proportional to exp(-|r|^2 / (2 ell^2)), a Gaussian of the std of two such kernels -- then set to mean 0
+    and standard deviation `std` over the realisation.  Shape (nz, ny, nx)."""
     nx, ny, nz = (int(d) for d in dims)
-    k, phi = grf_modes(seed, ell, modes)
-    x, y, z = node_coords(nx, h), node_coords(ny, h), node_coords(nz, h)
-    g = np.zeros((nz, ny, nx))
-    for m in range(modes):
-        ex = np.exp(1j * k[m, 0] * x)
-        ey = np.exp(1j * k[m, 1] * y)
-        ez = np.exp(1j * (k[m, 2] * z + phi[m]))
-        g += (ez[:, None, None] * ey[None, :, None] * ex[None, None, :]).real
-    g *= std * math.sqrt(2.0 / modes)
-    return np.exp(g)
+    w = normal(seed, 5, nx * ny * nz).reshape(nz, ny, nx)
+    s = ell / math.sqrt(2.0)
+    W = np.fft.rfftn(w)
+    W *= (_gauss_multiplier(nz, h, s)[:, None, None] * _gauss_multiplier(ny, h, s)[None, :, None]
+          * _gauss_multiplier(nx, h, s, real=True)[None, None, :])
+    g = np.fft.irfftn(W, s=(nz, ny, nx), axes=(0, 1, 2))
+    g -= g.mean()
+    sd = g.std()
+    if sd > 0:
+        g *= std / sd
+    return g
 
 
-def speed_grf_torch(dims: Sequence[int], h: float, seed: int, device, std: float = 0.5,
-                    ell: float = 0.05, modes: int = 64, dtype=None):
-    """The same field as speed_grf, evaluated with torch on `device` for grids too large for numpy.
+def speed_grf(dims: Sequence[int], h: float, seed: int, std: float = 0.5, ell: float = 0.05) -> np.ndarray:
+    """F = exp(g), g the Gaussian random field of grf_field (std `std`, correlation length `ell`)."""
+    return np.exp(grf_field(dims, h, seed, std, ell))
 
-    Values agree with speed_grf to rounding; tests that compare against the oracle
-    generate F with speed_grf instead.
-    """
+
+# ---- the same generators with torch (on a GPU for grids too large for the host's numpy) ----
+
+def _i64(c: int) -> int:
+    """An unsigned 64-bit constant as the signed int64 with the same bits."""
+    c &= 0xFFFFFFFFFFFFFFFF
+    return c - (1 << 64) if c >= (1 << 63) else c
+
+
+def splitmix64_torch(seed: int, stream: int, n: int, start: int, device):
+    """splitmix64's outputs as int64 tensors with the same bits (integer arithmetic wraps modulo 2^64;
+    the right shifts are made logical by masking)."""
+    import torch
+    key = _i64(seed * 0x100000001B3 + stream * 0x2545F4914F6CDD1D)
+    z = torch.arange(start + 1, start + n + 1, dtype=torch.int64, device=device)
+    z = z * _i64(0x9E3779B97F4A7C15) + key
+    z = (z ^ ((z >> 30) & ((1 << 34) - 1))) * _i64(0xBF58476D1CE4E5B9)
+    z = (z ^ ((z >> 27) & ((1 << 37) - 1))) * _i64(0x94D049BB133111EB)
+    return z ^ ((z >> 31) & ((1 << 33) - 1))
+
+
+def normal_torch(seed: int, stream: int, n: int, device, chunk: int = 1 << 25):
+    """normal(seed, stream, n) computed with torch in float64 on `device` (the same uniforms, bit for bit;
+    the Box-Muller transform agrees to rounding)."""
+    import torch
+    m = (n + 1) // 2
+    out = torch.empty(2 * m, dtype=torch.float64, device=device)
+    for p0 in range(0, m, chunk):
+        p1 = min(m, p0 + chunk)
+        z = splitmix64_torch(seed, stream, 2 * (p1 - p0), 2 * p0, device)
+        u = ((z >> 11) & ((1 << 53) - 1)).to(torch.float64) * (2.0 ** -53)
+        del z
+        u1 = 1.0 - u[0::2]
+        u2 = u[1::2]
+        rad = torch.sqrt(-2.0 * torch.log(u1))
+        out[2 * p0:2 * p1:2] = rad * torch.cos(2.0 * math.pi * u2)
+        out[2 * p0 + 1:2 * p1:2] = rad * torch.sin(2.0 * math.pi * u2)
+    return out[:n]
+
+
+def speed_grf_torch(dims: Sequence[int], h: float, seed: int, device, std: float = 0.5, ell: float = 0.05,
+                    dtype=None):
+    """speed_grf computed with torch on `device` (float64 arithmetic, the result in `dtype`, float32 by
+    default).  Values agree with speed_grf to rounding; tests that compare against the oracle generate F
+    with one of the two and hand the same values to both sides."""
     import torch
     nx, ny, nz = (int(d) for d in dims)
-    k, phi = grf_modes(seed, ell, modes)
-    dt = torch.float64
-    x = torch.arange(nx, device=device, dtype=dt) * h
-    y = torch.arange(ny, device=device, dtype=dt) * h
-    z = torch.arange(nz, device=device, dtype=dt) * h
-    out = torch.zeros((nz, ny, nx), device=device, dtype=torch.float32 if dtype is None else dtype)
-    # accumulate slab by slab in float64 to bound the temporary size
-    slab = max(1, (1 << 26) // max(1, nx * ny))
-    for z0 in range(0, nz, slab):
-        zz = z[z0:z0 + slab]
-        g = torch.zeros((zz.numel(), ny, nx), device=device, dtype=dt)
-        for m in range(modes):
-            g += torch.cos(k[m, 2] * zz[:, None, None] + k[m, 1] * y[None, :, None]
-                           + k[m, 0] * x[None, None, :] + phi[m])
-        g *= std * math.sqrt(2.0 / modes)
-        out[z0:z0 + slab] = torch.exp(g).to(out.dtype)
+    s = ell / math.sqrt(2.0)
+    w = normal_torch(seed, 5, nx * ny * nz, device).reshape(nz, ny, nx)
+    W = torch.fft.rfftn(w)
+    del w
+    mult = lambda n, real=False: torch.from_numpy(_gauss_multiplier(n, h, s, real)).to(device)
+    W *= mult(nz)[:, None, None] * mult(ny)[None, :, None] * mult(nx, True)[None, None, :]
+    g = torch.fft.irfftn(W, s=(nz, ny, nx))
+    del W
+    g -= g.mean()
+    sd = g.std(unbiased=False)
+    if float(sd) > 0:
+        g *= std / sd
+    out = torch.exp(g).to(torch.float32 if dtype is None else dtype)
+    del g
+    if out.is_cuda:
+        torch.cuda.empty_cache()
     return out
 
 
