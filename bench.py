@@ -37,8 +37,8 @@ KERNELS_PER_SOLVE = 4                                # gather_r, init_sources, r
 # capture of the same workload family at 512^3 (dram__bytes_read.sum + dram__bytes_write.sum = 9.387 GB +
 # 4.636 GB; smsp__inst_executed.sum = 23.517 G over 512^3 nodes), scaled to the launch by its node count;
 # profiles/k_restart_loop_c4_512_fixed2h.md gives the command.
-NCU_TRAFFIC_PER_NODE = {"fp32": (9.454e9 + 4.670e9) / 512 ** 3}
-NCU_INST_PER_NODE = {"fp32": 23.533e9 / 512 ** 3}
+NCU_TRAFFIC_PER_NODE = {"fp32": (9.436e9 + 4.657e9) / 512 ** 3}
+NCU_INST_PER_NODE = {"fp32": 23.852e9 / 512 ** 3}
 ISSUE_PER_SM_CYCLE = 4          # warp schedulers per SM, one warp instruction per cycle each
 
 
