@@ -456,11 +456,22 @@ def run_ours(args):
         for c in ctxs:
             eik.eik_destroy(c)
         nb = Fd.element_size() * w.npoints
+        # the copy engines alone: one plain pinned upload and download of the same bytes
+        cps = {}
+        for name, dst, src in (("h2d", Fd, Fh), ("d2h", outs[0], Fd)):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            dst.copy_(src, non_blocking=True)
+            b.record()
+            torch.cuda.synchronize()
+            cps[name] = nb / (a.elapsed_time(b) * 1e-3) / 1e9
         e2e = {"value": job_rate(w.npoints, args.e2e_steps, ws, e2e_s), "unit": "Mpoints/s",
                "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb, "steps": args.e2e_steps,
                "pipeline": "two contexts on two streams: host copies of one overlap the other's solve",
                "first_solve_ms": (marks[0] - t0) * 1e3 if marks else None,
                "step_ms_median": float(np.median(gaps)) if len(gaps) else None,
+               "step_ms": [round(float(g), 1) for g in gaps],
+               "h2d_gbs": cps["h2d"], "d2h_gbs": cps["d2h"],
                "last_copy_ms": (t1 - marks[-1]) * 1e3 if marks else None}
 
     # accuracy of this run's path against the FP64 oracle: the timed solve itself, every node, against the
