@@ -216,3 +216,49 @@ def test_waits_give_up_and_the_context_stays_usable(eik, orc):
     finally:
         eik.eik_destroy(ctx)
     assert_fp32_parity(psi, orc.fmm(F, w.h, w.sources))
+
+
+@pytest.mark.parametrize("frac", [0.3, 0.7])
+def test_width_band(eik, orc, frac):
+    """width_band (Alg. 6) with 32^3 blocks: exact (the 8^3 full solve's values, bit for bit) wherever the
+    solution is at most the width, tentative upper bounds above it."""
+    w = synth.workload("C4", 80)
+    F = synth.round_to(w.speed(), "fp32")
+    full = orc.fmm(F, w.h, w.sources)
+    width = frac * float(full[np.isfinite(full)].max())
+    Fh = np.ascontiguousarray(F.astype(np.float32))
+    ctx = eik.eik_create(w.dims, w.h, Fh, "fp32")
+    try:
+        eik.eik_add_sources(ctx, w.sources)
+        p8, _ = solve(eik, ctx, F.shape, 2 * w.h, block_dim=8)
+        for s in (1.0, 4.0, math.inf):
+            psi, st = solve(eik, ctx, F.shape, s * w.h, block_dim=32, width=width)
+            assert st["final_bound"] <= width
+            low = p8 <= width
+            assert np.array_equal(psi[low], p8[low]), s
+            assert np.all(psi[~low] >= p8[~low]), s
+    finally:
+        eik.eik_destroy(ctx)
+
+
+def test_async_solve_and_result(eik):
+    """eik_solve_async / eik_wait / eik_result_async with 32^3 blocks: the same psi as the synchronous calls,
+    with a 32^3 solve and an 8^3 solve on the same context in turn."""
+    import torch
+    w = synth.workload("C2", 72)
+    F = np.ascontiguousarray(w.speed().astype(np.float32))
+    ctx = eik.eik_create(w.dims, w.h, F, "fp32")
+    try:
+        eik.eik_add_sources(ctx, w.sources)
+        ref, _ = solve(eik, ctx, F.shape, 2 * w.h, block_dim=32)
+        outs = [torch.empty(F.shape, dtype=torch.float32, pin_memory=True) for _ in range(2)]
+        for i, bd in enumerate((32, 8)):
+            eik.eik_solve_async(ctx, 3 * w.h, block_dim=bd)
+            st = eik.eik_wait(ctx)
+            assert st["block_dim"] == bd
+            eik.eik_result_async(ctx, outs[i].numpy())
+            eik.eik_sync(ctx)
+        for o in outs:
+            assert np.array_equal(o.numpy().astype(np.float64), ref)
+    finally:
+        eik.eik_destroy(ctx)
