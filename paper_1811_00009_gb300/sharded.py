@@ -151,14 +151,20 @@ class Transport:
 
 class DistTransport(Transport):
     """torch.distributed point-to-point sends to the neighbouring ranks and an all-reduce (one process per
-    GPU with NCCL; gloo for host tensors)."""
+    GPU with NCCL).  With `staging`, device buffers travel through host memory (gloo) and arrive back on
+    the device they left."""
 
-    def __init__(self, rank: int, nranks: int, device=None):
-        self.rank, self.nranks, self.device = rank, nranks, device
+    def __init__(self, rank: int, nranks: int, device=None, staging: bool = False):
+        self.rank, self.nranks, self.device, self.staging = rank, nranks, device, staging
 
     def exchange(self, down, up):
         import torch
         import torch.distributed as dist
+        home = None
+        if self.staging:
+            home = (down if down is not None else up).device
+            down = down.cpu() if down is not None else None
+            up = up.cpu() if up is not None else None
         ops, got_below, got_above = [], None, None
         if self.rank > 0:
             got_below = torch.empty_like(down)
@@ -169,12 +175,15 @@ class DistTransport(Transport):
         if ops:
             for req in dist.batch_isend_irecv(ops):
                 req.wait()
+        if self.staging:
+            got_below = got_below.to(home) if got_below is not None else None
+            got_above = got_above.to(home) if got_above is not None else None
         return got_below, got_above
 
     def allreduce_sum(self, x: int) -> int:
         import torch
         import torch.distributed as dist
-        t = torch.tensor([int(x)], dtype=torch.int64, device=self.device)
+        t = torch.tensor([int(x)], dtype=torch.int64, device="cpu" if self.staging else self.device)
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
         return int(t.item())
 

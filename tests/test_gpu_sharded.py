@@ -117,3 +117,56 @@ def test_slab_calls_out_of_order(eik):
         eik.eik_slab_end(ctx)
     finally:
         eik.eik_destroy(ctx)
+
+
+def _rank_main(rank, world, port, n, q):
+    import os
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import paper_1811_00009_gb300 as E
+        from paper_1811_00009_gb300.sharded import DistTransport, Slab, run_rank, slab_parts
+        w = synth.workload("C4", n)
+        F = torch.from_numpy(synth.round_to(w.speed(), "fp32")).to("cuda", torch.float32)
+        part = slab_parts(n, world)[rank]
+        slab = Slab(E, w.dims, w.h, F[part.zlo:part.zhi].contiguous(), part, w.sources)
+        try:
+            k = run_rank(slab, DistTransport(rank, world, staging=True), 2 * w.h)
+            q.put((rank, slab.result_own().cpu().numpy(), k))
+        finally:
+            slab.close()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_ranks_as_processes(eik):
+    """Two processes, one slab each (on this one GPU), faces exchanged by torch.distributed through host
+    memory: the lockstep of sharded.run_rank with real slabs; the result equals the one-grid solve bit for
+    bit.  (The slab launches never wait on one another: each restart's launch ends by itself, and the two
+    processes' launches share the GPU in turn.)"""
+    import socket
+    import torch
+    import torch.multiprocessing as mp
+    n, world = 64, 2
+    w = synth.workload("C4", n)
+    F = torch.from_numpy(synth.round_to(w.speed(), "fp32")).to("cuda", torch.float32)
+    ref, st = one_grid(eik, w, F, 2 * w.h, "fp32")
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, n, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=300) for _ in range(world)), key=lambda r: r[0])
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    got = np.concatenate([r[1] for r in res], axis=0)
+    assert got.shape == ref.shape
+    assert np.array_equal(got, ref)
+    assert res[0][2] == res[1][2] and res[0][2] >= st["restarts"] - 1
