@@ -23,15 +23,11 @@
 // A march at restart k reads its block's latest copy and the neighbours'
 // copies as of the end of restart k-1 and writes the other copy, as the 8^3
 // path does, so no CTA reads memory written in the same restart.
-#include "eik.h"
-#include "eik_host.h"
 #include "eik_internal.cuh"
 #include "eik_march.cuh"
 
 #include <algorithm>
-#include <cmath>
 #include <cstdint>
-#include <vector>
 
 namespace eikg {
 namespace b32 {
@@ -685,7 +681,6 @@ __global__ void k_result32(const float* __restrict__ copy, const unsigned long l
 // ---------------------------------------------------------------------------
 // Host side (called from eik_runtime.cu)
 // ---------------------------------------------------------------------------
-size_t block32_smem_bytes() { return sizeof(b32::Smem); }
 int block32_edge_values() { return b32::kCopy; }
 
 cudaError_t block32_occupancy(int* per_sm) {

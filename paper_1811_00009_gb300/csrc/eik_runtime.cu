@@ -39,7 +39,6 @@ cudaError_t launch_slab_export(const T*, const unsigned long long*, const unsign
 template <typename T>
 cudaError_t launch_slab_import(T*, unsigned long long*, unsigned long long*, int, int, int, int, const void*, int,
                                int32_t*, int64_t, Ctrl*, int32_t*, cudaStream_t);
-size_t block32_smem_bytes();
 int block32_edge_values();
 cudaError_t block32_occupancy(int* per_sm);
 cudaError_t block32_layout(const float*, int, int, int, float*, int, int, int64_t, cudaStream_t);
