@@ -422,3 +422,23 @@ def test_device_waits_give_up_and_the_context_stays_usable(eik, orc, kw):
     finally:
         eik.eik_destroy(ctx)
     assert_parity(psi.astype(np.float64), orc.fmm(F.astype(np.float32).astype(np.float64), w.h, w.sources), "fp32")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_many_sources(eik, orc, precision):
+    """200 random point sources on a ragged grid: many bricks and 32^3 blocks hold several fixed nodes, some
+    source cells overlap (the smaller distance wins, Alg. 1); every block edge gives the oracle's solution."""
+    dims = (67, 45, 53)
+    h = synth.grid_h(dims)
+    F = synth.round_to(0.5 + synth.uniform(41, 1, int(np.prod(dims))).reshape(dims[::-1]), precision)
+    src = synth.random_sources(77, 3, dims, h, 200)
+    ref = orc.fmm(F, h, src)
+    blocks = (8, 16, 32) if precision == "fp32" else (8, 16)
+    outs = []
+    for bd in blocks:
+        psi, st = run(eik, F, h, src, precision, 2 * h, block_dim=bd)
+        assert st["status"] == 0
+        assert_parity(psi, ref, precision)
+        outs.append(psi)
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
