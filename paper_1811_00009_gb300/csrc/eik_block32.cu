@@ -50,7 +50,8 @@ struct Params {
     unsigned long long* stamp;
     const float* rr;
     int32_t* queued;                   // kRing x nblk
-    int32_t* list[kRing];
+    int32_t* list[kRing];              // work lists by ring slot; entries not yet written are -1
+    int32_t* done;                     // per block: last restart whose march of it finished (-1: none)
     Ctrl* ctrl;
     float window;                      // omega: acceptance window = omega * min(h/F) over the block
     float tau;                         // FP64 root fallback threshold
@@ -483,7 +484,67 @@ __device__ void march32(const Params& P, Smem& S, int32_t blk, int k, float bpre
         const int fm = S.facemask;
         for (int f = 0; f < 6; ++f)
             if (((fm >> f) & 1) && nbr[f] >= 0) enqueue(P, k, nbr[f]);
+        // publish: the block's restart-k march has finished (read by early marches
+        // of its neighbours; the CTA barriers above put every thread's writes before it)
+        __threadfence();
+        st_release(P.done + blk, k);
     }
+}
+
+// At the start of restart k every thread of the launch clears its share of the
+// list restart k-1 used (ring slot (k-1) mod kRing) to -1.  That slot is next
+// written by early marches of restart k+2, after the barrier of restart k.
+__device__ __forceinline__ void clear_used32(const Params& P, int k) {
+    const int sp = (k + kRing - 1) % kRing;
+    const int m = __ldcg(&P.ctrl->used[sp]);
+    int32_t* list = P.list[sp];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) list[i] = -1;
+}
+
+// Thread 0 of a CTA waiting at the barrier of restart k: claim an entry of
+// restart k+1's list (only below its current length, so an entry is claimed
+// only once it has been counted), wait until the enqueuer has written it, then
+// until the block and each of its six neighbours that is on restart k's list
+// have finished that march.  An early march then reads what it would read after
+// the barrier.  Returns the block, -1 if there is nothing to claim, -2 if a
+// wait ran out (bounded).
+__device__ int32_t early_claim32(const Params& P, int k) {
+    Ctrl* C = P.ctrl;
+    const int s = k % kRing, s1 = (k + 1) % kRing;
+    int h = __ldcg(&C->head[s1]);
+    int i = -1;
+    for (int tries = 0; tries < 64; ++tries) {
+        if (h >= __ldcg(&C->count[s1])) return -1;
+        const int prev = atomicCAS(&C->head[s1], h, h + 1);
+        if (prev == h) {
+            i = h;
+            break;
+        }
+        h = prev;
+    }
+    if (i < 0) return -1;
+    int32_t b = ld_acquire(P.list[s1] + i);
+    for (long long it = 0; b < 0; ++it) {
+        if (it > P.wait_limit) return -2;
+        __nanosleep(32);
+        b = ld_acquire(P.list[s1] + i);
+    }
+    const int bx = static_cast<int>(b % P.NBX), by = static_cast<int>((b / P.NBX) % P.NBY);
+    const int bz = static_cast<int>(b / (static_cast<int64_t>(P.NBX) * P.NBY));
+    const int32_t plane = P.NBX * P.NBY;
+    const int32_t xs[7] = {b, bx > 0 ? b - 1 : -1, bx < P.NBX - 1 ? b + 1 : -1, by > 0 ? b - P.NBX : -1,
+                           by < P.NBY - 1 ? b + P.NBX : -1, bz > 0 ? b - plane : -1, bz < P.NBZ - 1 ? b + plane : -1};
+    for (int j = 0; j < 7; ++j) {
+        const int32_t x = xs[j];
+        if (x < 0 || __ldcg(P.queued + static_cast<int64_t>(s) * P.nblk + x) != k) continue;
+        unsigned nap = 64;
+        for (long long it = 0; ld_acquire(P.done + x) < k; ++it) {
+            if (it > P.wait_limit) return -2;
+            __nanosleep(nap);
+            if (nap < 1024) nap <<= 1;
+        }
+    }
+    return b;
 }
 
 // Bookkeeping at the end of restart k (thread 0 of the CTA that reaches the
@@ -523,8 +584,10 @@ __device__ void restart_end32(const Params& P) {
 // The restart loop of Alg. 6 for 32^3 blocks: one persistent cooperative
 // launch, one CTA of 1024 threads per SM; each restart every CTA takes blocks
 // from the work list and marches them; one grid barrier (one arrival per CTA)
-// ends the restart.  Every wait is bounded and CTA-uniform: thread 0 polls,
-// and the CTA leaves as a whole when a wait runs out.
+// ends the restart, and a CTA waiting there marches blocks of restart k+1 whose
+// neighbourhood has finished restart k (the stride is fixed, so the next bound
+// is known).  Every wait is bounded and CTA-uniform: thread 0 polls, writes the
+// outcome to shared memory, and the whole CTA acts on it after a barrier.
 __global__ void __launch_bounds__(kT, 1) k_loop32(Params P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem& S = *reinterpret_cast<Smem*>(smem_raw);
@@ -540,8 +603,11 @@ __global__ void __launch_bounds__(kT, 1) k_loop32(Params P) {
         const int k = __ldcg(&C->k);
         const int s = k % kRing;
         const double bd = __ldcg(&C->bound), bp = __ldcg(&C->bound_prev);
-        const float bound = __double2float_rd(bd), bprev = __double2float_rd(bp);
-        const bool grow = bd < P.width;
+        const double bn = fmin(bd + __ldcg(&C->stride), P.width);      // restart k+1's bound
+        const float bound = __double2float_rd(bd), bprev = __double2float_rd(bp), bnext = __double2float_rd(bn);
+        const bool grow = bd < P.width, grow_next = bn < P.width;
+        clear_used32(P, k);
+        // restart k's list
         for (;;) {
             if (t == 0) {
                 const int i = atomicAdd(&C->head[s], 1);
@@ -553,43 +619,65 @@ __global__ void __launch_bounds__(kT, 1) k_loop32(Params P) {
             march32(P, S, blk, k, bprev, bound, grow);
             __syncthreads();
         }
+        // the grid barrier; state 0: waiting, 1: released, 2: leave the loop
+        unsigned gen = 0;
+        long long polls = 0;
+        unsigned nap = 32;
         if (t == 0) {
-            int state = 0;
-            const unsigned gen = ld_acquire(&C->bar_gen);
+            gen = ld_acquire(&C->bar_gen);
             __threadfence();
+            int state = 0;
             if (atomicAdd(&C->bar_count, 1u) == gridDim.x - 1) {
                 __threadfence();
                 restart_end32(P);
                 C->bar_count = 0;
                 __threadfence();
                 st_release(&C->bar_gen, gen + 1);
-                state = 1;
-            } else {
-                unsigned nap = 32;
-                for (long long it = 0;; ++it) {
-                    if (ld_acquire(&C->bar_gen) != gen) {
-                        state = 1;
-                        break;
-                    }
-                    if (__ldcg(&C->status) & kStWaitTimeout) {
-                        state = 2;
-                        break;
-                    }
-                    if (it > P.wait_limit) {
-                        atomicOr(&C->status, kStWaitTimeout);
-                        __threadfence();
-                        state = 2;
-                        break;
-                    }
-                    __nanosleep(nap);
-                    if (nap < 2048) nap <<= 1;
-                }
+                state = __ldcg(&C->done) ? 2 : 1;
             }
-            s_state = (state == 2 || __ldcg(&C->done)) ? 2 : 1;
+            s_state = state;
+            s_blk = -1;
         }
         __syncthreads();
-        if (s_state == 2) return;
-        __syncthreads();          // every thread has read s_state before thread 0 writes s_blk again
+        int state = s_state;
+        __syncthreads();          // every thread has read s_state before thread 0 writes it again
+        while (state == 0) {
+            if (t == 0) {
+                int st = 0;
+                int32_t b = -1;
+                if (ld_acquire(&C->bar_gen) != gen) {
+                    st = __ldcg(&C->done) ? 2 : 1;
+                } else if (__ldcg(&C->status) & kStWaitTimeout) {
+                    st = 2;
+                } else if (++polls > P.wait_limit) {
+                    atomicOr(&C->status, kStWaitTimeout);
+                    __threadfence();
+                    st = 2;
+                } else {
+                    b = early_claim32(P, k);
+                    if (b == -2) {
+                        atomicOr(&C->status, kStWaitTimeout);
+                        __threadfence();
+                        st = 2;
+                        b = -1;
+                    } else if (b >= 0) {
+                        polls = 0;
+                        nap = 32;
+                    } else {
+                        __nanosleep(nap);
+                        if (nap < 2048) nap <<= 1;
+                    }
+                }
+                s_state = st;
+                s_blk = b;
+            }
+            __syncthreads();
+            state = s_state;
+            const int32_t blk = s_blk;
+            __syncthreads();      // read before thread 0 writes again
+            if (state == 0 && blk >= 0) march32(P, S, blk, k + 1, bound, bnext, grow_next);
+        }
+        if (state == 2) return;
     }
 }
 
@@ -724,9 +812,9 @@ cudaError_t block32_result(const float* copy, const unsigned long long* stamp, f
 }
 
 cudaError_t block32_loop(int NBX, int NBY, int NBZ, int64_t nblk, float* copy, unsigned* ups,
-                         unsigned long long* stamp, const float* rr, int32_t* queued, int32_t* lists, Ctrl* ctrl,
-                         float window, float tau, double width, int64_t max_restarts, long long wait_limit, int grid,
-                         cudaStream_t s) {
+                         unsigned long long* stamp, const float* rr, int32_t* queued, int32_t* lists, int32_t* done,
+                         Ctrl* ctrl, float window, float tau, double width, int64_t max_restarts,
+                         long long wait_limit, int grid, cudaStream_t s) {
     b32::Params P{};
     P.NBX = NBX;
     P.NBY = NBY;
@@ -738,6 +826,7 @@ cudaError_t block32_loop(int NBX, int NBY, int NBZ, int64_t nblk, float* copy, u
     P.rr = rr;
     P.queued = queued;
     for (int r = 0; r < kRing; ++r) P.list[r] = lists + static_cast<int64_t>(r) * nblk;
+    P.done = done;
     P.ctrl = ctrl;
     P.window = window;
     P.tau = tau;

@@ -47,7 +47,7 @@ cudaError_t block32_init(int, const int32_t*, const int32_t*, const double*, int
 cudaError_t block32_restore(int, const int32_t*, const int32_t*, const float*, float*, cudaStream_t);
 cudaError_t block32_result(const float*, const unsigned long long*, float*, int, int, int, int, int, cudaStream_t);
 cudaError_t block32_loop(int, int, int, int64_t, float*, unsigned*, unsigned long long*, const float*, int32_t*,
-                         int32_t*, Ctrl*, float, float, double, int64_t, long long, int, cudaStream_t);
+                         int32_t*, int32_t*, Ctrl*, float, float, double, int64_t, long long, int, cudaStream_t);
 template <typename T>
 size_t loop_smem_bytes();
 template <typename T>
@@ -132,6 +132,7 @@ struct eik_ctx {
         unsigned long long* stamp = nullptr;
         int32_t* queued = nullptr;
         int32_t* lists = nullptr;
+        int32_t* done = nullptr;
         bool rr_valid = false;
         int grid = 0;
     } b32;
@@ -166,7 +167,7 @@ void free_all(eik_ctx* c) {
                     c->ctrl,  c->log, c->scratch, c->fstage, c->d_mlp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    void* p32[] = {c->b32.rr, c->b32.copy, c->b32.ups, c->b32.stamp, c->b32.queued, c->b32.lists};
+    void* p32[] = {c->b32.rr, c->b32.copy, c->b32.ups, c->b32.stamp, c->b32.queued, c->b32.lists, c->b32.done};
     for (void* p : p32)
         if (p) cudaFree(p);
     if (c->h_err) cudaFreeHost(c->h_err);
@@ -701,6 +702,7 @@ eik_status queue_solve32(eik_ctx* c, const eik_params& P) {
             {reinterpret_cast<void**>(&B.stamp), nb * sizeof(unsigned long long)},
             {reinterpret_cast<void**>(&B.queued), eikg::kRing * nb * sizeof(int32_t)},
             {reinterpret_cast<void**>(&B.lists), eikg::kRing * nb * sizeof(int32_t)},
+            {reinterpret_cast<void**>(&B.done), nb * sizeof(int32_t)},
         };
         for (auto& a : allocs) {
             const cudaError_t e = dalloc(a.p, a.bytes);
@@ -812,6 +814,8 @@ eik_status queue_solve32(eik_ctx* c, const eik_params& P) {
     const size_t nb = static_cast<size_t>(B.nblk);
     EIK_CK(c, cudaMemsetAsync(B.stamp, 0xFF, nb * sizeof(unsigned long long), s));
     EIK_CK(c, cudaMemsetAsync(B.queued, 0xFF, eikg::kRing * nb * sizeof(int32_t), s));
+    EIK_CK(c, cudaMemsetAsync(B.lists, 0xFF, eikg::kRing * nb * sizeof(int32_t), s));
+    EIK_CK(c, cudaMemsetAsync(B.done, 0xFF, nb * sizeof(int32_t), s));
     if (nfix > 0)
         EIK_CK(c, eikg::block32_init(nfix, c->d_fix_b, c->d_fix_p, d_fv, static_cast<int>(sb.size()), d_sb,
                                      static_cast<int>(enq.size()), d_enq, B.copy, B.ups, B.stamp, B.queued + nb, B.rr,
@@ -831,7 +835,8 @@ eik_status queue_solve32(eik_ctx* c, const eik_params& P) {
     EIK_CK(c, cudaMemcpyAsync(c->ctrl, &H, sizeof(H), cudaMemcpyHostToDevice, s));
     if (!enq.empty()) {
         if (P.loop_events[0]) EIK_CK(c, cudaEventRecord(static_cast<cudaEvent_t>(P.loop_events[0]), s));
-        EIK_CK(c, eikg::block32_loop(B.NBX, B.NBY, B.NBZ, B.nblk, B.copy, B.ups, B.stamp, B.rr, B.queued, B.lists, c->ctrl,
+        EIK_CK(c, eikg::block32_loop(B.NBX, B.NBY, B.NBZ, B.nblk, B.copy, B.ups, B.stamp, B.rr, B.queued, B.lists, B.done,
+                                     c->ctrl,
                                      static_cast<float>(P.window), static_cast<float>(P.fallback_tau), P.width,
                                      P.max_restarts, P.wait_polls > 0 ? P.wait_polls : eikg::kWaitPolls, B.grid, s));
         if (P.loop_events[1]) EIK_CK(c, cudaEventRecord(static_cast<cudaEvent_t>(P.loop_events[1]), s));
