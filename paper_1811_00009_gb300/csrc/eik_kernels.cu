@@ -513,6 +513,61 @@ __global__ void k_result(const T* __restrict__ slot, const unsigned long long* _
     }
 }
 
+// FP32 with x-rows of a multiple of 4 nodes and 16-byte aligned buffers: the
+// same two kernels moving four consecutive nodes per thread (one 16-byte load
+// and store each; four nodes never straddle a brick row).
+__global__ void k_layout_speed_x4(const float* __restrict__ F, float* __restrict__ rr, int nx, int ny, int nz,
+                                  int BX, int BY, int64_t nbricks, float hT, int* err, int seq) {
+    const float INF = __int_as_float(0x7f800000);
+    const int px = BX * 8, py = BY * 8;
+    const int64_t rows = (nbricks / (static_cast<int64_t>(BX) * BY)) * 8 * py;
+    int bad = 0;
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int k = static_cast<int>(r / py), j = static_cast<int>(r - static_cast<int64_t>(k) * py);
+        const bool inrow = j < ny && k < nz;
+        const int64_t frow = inrow ? (static_cast<int64_t>(k) * ny + j) * nx : 0;
+        float* out = rr + ((static_cast<int64_t>(k >> 3) * BY + (j >> 3)) * BX) * kBrick + ((k & 7) * 8 + (j & 7)) * 8;
+        for (int i = 4 * threadIdx.x; i < px; i += 4 * blockDim.x) {
+            float4 v = make_float4(INF, INF, INF, INF);
+            if (inrow && i < nx) {
+                const float4 f = __ldg(reinterpret_cast<const float4*>(F + frow + i));
+                const float fq[4] = {f.x, f.y, f.z, f.w};
+                float vq[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    vq[e] = INF;
+                    if (!(fq[e] >= 0.0f) || !(fq[e] < INF)) bad = 1;
+                    else if (fq[e] > 0.0f) vq[e] = hT / fq[e];
+                }
+                v = make_float4(vq[0], vq[1], vq[2], vq[3]);
+            }
+            __stcs(reinterpret_cast<float4*>(out + (i >> 3) * kBrick + (i & 7)), v);
+        }
+    }
+    if (bad) *reinterpret_cast<volatile int*>(err) = seq;
+}
+
+__global__ void k_result_x4(const float* __restrict__ slot, const unsigned long long* __restrict__ stamp,
+                            float* __restrict__ out, int nx, int ny, int z_begin, int z_end, int BX, int BY) {
+    const float INF = __int_as_float(0x7f800000);
+    const int rows = ny * (z_end - z_begin);
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int kk = r / ny, j = r - kk * ny, k = z_begin + kk;
+        const int64_t brow = (static_cast<int64_t>(k >> 3) * BY + (j >> 3)) * BX;
+        const int prow = ((k & 7) * 8 + (j & 7)) * 8;
+        float* o = out + static_cast<int64_t>(r) * nx;
+        for (int i = 4 * threadIdx.x; i < nx; i += 4 * blockDim.x) {
+            const int64_t b = brow + (i >> 3);
+            const unsigned long long st = __ldg(stamp + b);
+            const float4 v = (st == kUntouched)
+                                 ? make_float4(INF, INF, INF, INF)
+                                 : __ldcs(reinterpret_cast<const float4*>(slot + (b * 2 + stamp_copy(st)) * kSlot +
+                                                                          prow + (i & 7)));
+            *reinterpret_cast<float4*>(o + i) = v;
+        }
+    }
+}
+
 // A grid sharded in z across GPUs: the face layer of every brick of plane bz
 // that a neighbouring GPU's bricks read (face 4: the z = 0 layer, read by the
 // GPU below; face 5: the z = 7 layer, read by the GPU above), with the Upsilon
@@ -578,6 +633,13 @@ cudaError_t launch_layout_speed(const T* F, T* rr, int nx, int ny, int nz, int B
     const int64_t rows = (nbricks / (static_cast<int64_t>(BX) * BY)) * 8 * (static_cast<int64_t>(BY) * 8);
     int grid = static_cast<int>(rows < 65535 * 4 ? rows : 65535 * 4);
     if (grid < 1) grid = 1;
+    if constexpr (sizeof(T) == 4) {
+        if (nx % 4 == 0 && reinterpret_cast<uintptr_t>(F) % 16 == 0) {
+            k_layout_speed_x4<<<grid, 256, 0, s>>>(reinterpret_cast<const float*>(F), reinterpret_cast<float*>(rr), nx,
+                                                   ny, nz, BX, BY, nbricks, static_cast<float>(h), err, seq);
+            return cudaGetLastError();
+        }
+    }
     k_layout_speed<T><<<grid, 256, 0, s>>>(F, rr, nx, ny, nz, BX, BY, nbricks, h, err, seq);
     return cudaGetLastError();
 }
@@ -618,6 +680,13 @@ cudaError_t launch_result(const T* slot, const unsigned long long* stamp, T* out
     const int64_t rows = static_cast<int64_t>(ny) * (z_end - z_begin);
     int grid = static_cast<int>(rows < 65535 * 4 ? rows : 65535 * 4);
     if (grid < 1) grid = 1;
+    if constexpr (sizeof(T) == 4) {
+        if (nx % 4 == 0 && reinterpret_cast<uintptr_t>(out) % 16 == 0) {
+            k_result_x4<<<grid, 256, 0, s>>>(reinterpret_cast<const float*>(slot), stamp, reinterpret_cast<float*>(out),
+                                             nx, ny, z_begin, z_end, BX, BY);
+            return cudaGetLastError();
+        }
+    }
     k_result<T><<<grid, 256, 0, s>>>(slot, stamp, out, nx, ny, z_begin, z_end, BX, BY);
     return cudaGetLastError();
 }
