@@ -98,25 +98,26 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _worker(rank, world, port, n, sources, out):
+def _worker(rank, world, port, n, sources, out, staging=False):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         part = slab_parts(n, world)[rank]
         slab = LineSlab(part, n, sources)
-        k = run_rank(slab, DistTransport(rank, world), stride=1.0)
+        k = run_rank(slab, DistTransport(rank, world, staging=staging), stride=1.0)
         out.put((rank, part.z0, slab.own.tolist(), k, slab.log))
     finally:
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world,n,sources", [(2, 40, [3]), (3, 61, [0, 50]), (2, 17, [16])])
-def test_lockstep_exchange_over_gloo(world, n, sources):
+@pytest.mark.parametrize("world,n,sources,staging", [(2, 40, [3], False), (3, 61, [0, 50], False),
+                                                     (2, 17, [16], False), (3, 61, [0, 50], True)])
+def test_lockstep_exchange_over_gloo(world, n, sources, staging):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, world, port, n, sources, q)) for r in range(world)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, n, sources, q, staging)) for r in range(world)]
     for p in procs:
         p.start()
     res = sorted(q.get(timeout=120) for _ in range(world))
