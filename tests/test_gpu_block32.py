@@ -262,3 +262,23 @@ def test_async_solve_and_result(eik):
             assert np.array_equal(o.numpy().astype(np.float64), ref)
     finally:
         eik.eik_destroy(ctx)
+
+
+def test_restart_cap(eik, orc):
+    """max_restarts ends a 32^3 solve with EIK_ETIMEOUT (CTAs in an early march of the next restart finish
+    it and leave); the next solve on the context is correct."""
+    w = synth.workload("C4", 96)
+    F = synth.round_to(w.speed(), "fp32")
+    Fh = np.ascontiguousarray(F.astype(np.float32))
+    ctx = eik.eik_create(w.dims, w.h, Fh, "fp32")
+    try:
+        eik.eik_add_sources(ctx, w.sources)
+        for cap in (1, 3):
+            with pytest.raises(eik.EikError) as e:
+                eik.eik_solve_ex(ctx, w.h, block_dim=32, max_restarts=cap)
+            assert e.value.status == eik.EIK_ETIMEOUT and "restart cap" in str(e.value)
+        psi, st = solve(eik, ctx, F.shape, 2 * w.h, block_dim=32)
+        assert st["status"] == 0
+    finally:
+        eik.eik_destroy(ctx)
+    assert_fp32_parity(psi, orc.fmm(F, w.h, w.sources))
