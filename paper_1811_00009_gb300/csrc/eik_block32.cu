@@ -6,7 +6,9 @@
 // 157 KB) fits one CTA's shared memory, and so do the bit masks of the march:
 // one 32-bit word per x-row of the block (y + 32 z) holds the row's band
 // (BAND of Sec. 2.1), the nodes accepted in a round, the nodes lowered in the
-// march (Upsilon) and the nodes that are solved at all.  Thread t owns row t.
+// march (Upsilon) and the nodes that are solved at all.  Thread t loads and
+// writes back row t; in the rounds the rows are dealt out diagonally (see
+// round_row) so that a front lying in a plane spreads over all warps.
 //
 // Data layout in HBM (one grid): blocks b = (bz*NBY + by)*NBX + bx of 32^3
 // nodes, node p = (z*32 + y)*32 + x; the ragged last block of each axis is
@@ -22,7 +24,10 @@
 //   stamp[b], queued, lists as for the 8^3 bricks (eik_internal.cuh)
 // A march at restart k reads its block's latest copy and the neighbours'
 // copies as of the end of restart k-1 and writes the other copy, as the 8^3
-// path does, so no CTA reads memory written in the same restart.
+// path does, so a march never reads what another march of its restart writes;
+// an early march of restart k+1 starts only once its block and neighbours have
+// finished restart k (their done marks), and then reads the same as after the
+// barrier.
 #include "eik_internal.cuh"
 #include "eik_march.cuh"
 
