@@ -290,7 +290,8 @@ def main():
     ap.add_argument("--eval-1024", action="store_true", help="also evaluate on the 1024^3 GRF workload")
     ap.add_argument("--quick", action="store_true", help="small data set (tests)")
     ap.add_argument("--sizes", default="192,256,320,384,448,512,640,768,1024",
-                    help="grid edges of the training grids (two seeds per family and edge)")
+                    help="grid edges of the training grids")
+    ap.add_argument("--seeds", type=int, default=2, help="seeds per family and edge (at most 10)")
     ap.add_argument("--runs-out", default=None, help="save the collected per-restart records (JSON)")
     ap.add_argument("--runs-in", default=None,
                     help="train from saved records instead of collecting (comma-separated files are merged)")
@@ -313,8 +314,9 @@ def main():
         grids = [("grf", 96, 21), ("layers", 96, 22)]
     else:
         sizes = [int(v) for v in args.sizes.split(",")]
-        grids = [(fam, n, 100 + 20 * i + 2 * j + r) for i, fam in enumerate(("sines", "layers", "grf"))
-                 for j, n in enumerate(sizes) for r in range(2)]
+        k = max(1, min(10, args.seeds))
+        grids = [(fam, n, 100 + 100 * i + k * j + r if k != 2 else 100 + 20 * i + 2 * j + r)
+                 for i, fam in enumerate(("sines", "layers", "grf")) for j, n in enumerate(sizes) for r in range(k)]
     t0 = time.time()
     if args.runs_in:
         runs = []
