@@ -66,3 +66,20 @@ def test_paper_case_fp32(eik, orc, case):
         assert np.array_equal(np.isfinite(psi), fin), (case, s)
         assert np.max(np.abs(psi[fin] - ref[fin])) <= 1e-5 * float(ref[fin].max()), (case, s)
         assert st["fallbacks"] == 0 or case == 3                 # Case 3's F nearly vanishes in places
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_case1_converges_to_the_exact_distance(eik, precision):
+    """The accuracy study of Sec. 3.2 for Case 1 (F = 1, centre source): the GPU solution's error against the
+    exact distance falls as the grid is refined, at the first-order scheme's rate (order 0.7-1 between
+    32^3, 64^3 and 128^3, the log factor of a point source keeping it below 1)."""
+    errs = []
+    for n in (32, 64, 128):
+        F, h, src = synth.speed_paper_case(1, n)
+        psi, st = solve(eik, F, h, src, precision, 2 * h, 8)
+        c = (np.arange(n) - 0.5 * (n - 1)) * h
+        exact = np.sqrt(c[None, None, :] ** 2 + c[None, :, None] ** 2 + c[:, None, None] ** 2)
+        errs.append(float(np.max(np.abs(psi - exact))))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(0.6 <= o <= 1.1 for o in orders), (errs, orders)
+    assert errs[-1] < 3.0 / 128, errs                  # about 2.4 h at 128^3
